@@ -1,0 +1,161 @@
+"""End-to-end pins for the oracle's SketchyCGAL (Alg. 6.1).
+
+* Loop invariants (Eq. 6.5 and Section 6.2.2) against CGAL with an explicit
+  matrix iterate fed the same directions (Alg. 3.1, dense, independent code).
+* The inexact LMO inequality (Eq. 6.1) along the trajectory.
+* Closed-form MaxCut SDP values on vertex-transitive graphs (golden file).
+* The certified bracket dual phi(y) <= p* <= <C, X_feasible> (Eq. E.2) against
+  brute-force max cuts and the Goemans-Williamson ratio.
+* Phase retrieval recovers the planted signal (Section 7.3, target 1e-2).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.cgal_dense import cgal_dense, dense_maxcut, dense_phase, scale_dense
+from oracle.problems import MaxCutProblem, PhaseProblem
+from oracle.rounding import brute_force_maxcut, phase_error, phase_round, round_maxcut, cut_weight, sgn
+from oracle.sketchycgal import sketchy_cgal
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "maxcut_closed_forms.json")
+
+
+def _graph(kind, n):
+    return W.cycle_graph(n) if kind == "cycle" else W.complete_graph(n)
+
+
+def _dual_value(prob, y_scaled):
+    """phi(y) = alpha lambda_min(C + A* y) - <y, b> on the original data (Eq. E.2)."""
+    y = y_scaled * prob.normC / prob.normA   # Lagrangian of Eq. 7.1 scaled back
+    n = prob.n
+    C = -0.25 * prob.L.toarray()
+    lam = np.linalg.eigvalsh(C + np.diag(y))[0]
+    return prob.alpha_orig * lam - float(np.dot(y, prob.b_orig))
+
+
+def _feasible_objective(prob, U, Lam):
+    """<C, X~> with X~ = diag(X^)^{-1/2} X^ diag(X^)^{-1/2}, a feasible point of Eq. 1.2."""
+    Xh = (U * Lam) @ U.T
+    d = np.sqrt(np.diag(Xh))
+    Xt = Xh / np.outer(d, d)
+    return float(np.sum(-0.25 * prob.L.toarray() * Xt))
+
+
+@pytest.mark.parametrize("scale", [True, False])
+@pytest.mark.parametrize("kind", ["maxcut", "phase"])
+def test_loop_invariants_against_dense_cgal(kind, scale):
+    T = 25
+    if kind == "maxcut":
+        g = W.er_graph(14, 30, seed=1, weights="pm1")
+        prob = MaxCutProblem(g.n, g.i, g.j, g.w, scale=scale)
+        C, As, b, alpha = dense_maxcut(g.n, g.i, g.j, g.w)
+        R = 4
+    else:
+        pd = W.phase_problem(8, 12, seed=1)
+        prob = PhaseProblem(pd.masks, pd.b, scale=scale)
+        C, As, b, alpha = dense_phase(pd.masks, pd.b)
+        R = 3
+    res = sketchy_cgal(prob, R=R, T=T, seed=4, record_v=True, trace_correct=False)
+    sc = scale_dense(C, As, b, alpha) if scale else dict(C=C, As=As, b=b, alpha=alpha)
+    flags = [h["h"] for h in res.history]
+    recs = cgal_dense(sc["C"], sc["As"], sc["b"], sc["alpha"], T, vs=res.vs, h_flags=flags,
+                      Omega=res.Omega)
+    last = recs[-1]
+    np.testing.assert_allclose(res.z, last["z"], rtol=1e-10, atol=1e-13)        # z = A X
+    np.testing.assert_allclose(res.S, last["S"], rtol=1e-10, atol=1e-13)        # S = X Omega
+    assert math.isclose(res.p, last["p"], rel_tol=1e-10, abs_tol=1e-13)         # p = <C, X>
+    assert math.isclose(res.tau, last["tau"], rel_tol=1e-10, abs_tol=1e-13)     # tau = tr X
+    np.testing.assert_allclose(res.y, last["y"], rtol=1e-9, atol=1e-12)         # same dual path
+    # the Ritz value xi_t is >= lambda_min(D_t) and v_t satisfies Eq. 6.1
+    for t, (h, rec) in enumerate(zip(res.history, recs), start=1):
+        D = rec["D"]
+        v = res.vs[t - 1]
+        vDv = float(np.real(np.vdot(v, D @ v)))
+        assert vDv <= rec["lam_min"] + rec["normD"] / math.sqrt(t + 1) + 1e-12
+        assert h["xi"] >= rec["lam_min"] - 1e-10 * max(1.0, rec["normD"])
+
+
+def _closed_form_cases():
+    return json.load(open(GOLDEN))["cases"]
+
+
+@pytest.mark.parametrize("case", _closed_form_cases(), ids=lambda c: f"{c['graph']}{c['n']}")
+def test_closed_form_sdp_values(case):
+    g = _graph(case["graph"], case["n"])
+    prob = MaxCutProblem(g.n, g.i, g.j, g.w)
+    res = sketchy_cgal(prob, R=4, T=3000, seed=0)
+    sdp = case["sdp"]
+    est = -res.history[-1]["p_orig"]
+    assert abs(est - sdp) / sdp < 2e-3
+    # weak duality on the original data: phi(y_T) <= p* = -sdp
+    assert _dual_value(prob, res.y) <= -sdp + 1e-9
+    # a feasible point cannot beat the optimum
+    assert _feasible_objective(prob, res.U, res.Lam) >= -sdp - 1e-9
+    # the rounded cut is a cut: never above the true max cut
+    best, _, _ = round_maxcut(res.U, g.i, g.j, g.w)
+    assert best <= case["maxcut"]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bracket_against_brute_force_maxcut(seed):
+    n = 14
+    g = W.er_graph(n, 30, seed=seed, weights="unit")
+    prob = MaxCutProblem(g.n, g.i, g.j, g.w)
+    mc = brute_force_maxcut(n, g.i, g.j, g.w)
+    res = sketchy_cgal(prob, R=5, T=1500, seed=seed)
+    upper = -_dual_value(prob, res.y)                    # SDP <= -phi(y)
+    lower = -_feasible_objective(prob, res.U, res.Lam)  # SDP >= -<C, X~>
+    assert upper >= mc - 1e-9                            # SDP >= max cut (relaxation, Eq. 1.2)
+    assert lower <= mc / 0.87856 + 1e-9                  # SDP <= max cut / 0.87856 (Goemans-Williamson)
+    assert lower <= upper + 1e-9
+    assert (upper - lower) / upper < 0.02                # the bracket has closed after T
+    best, _, _ = round_maxcut(res.U, g.i, g.j, g.w)
+    assert best <= mc
+
+
+def test_rounding_reading_and_integer_cuts():
+    g = W.er_graph(50, 200, seed=3, weights="pm1")
+    r = np.random.default_rng(0)
+    U = r.standard_normal((50, 3))
+    U[0, 1] = 0.0  # sgn(0) = +1
+    best, col, cuts = round_maxcut(U, g.i, g.j, g.w)
+    for c in range(3):
+        chi = np.where(U[:, c] >= 0, 1, -1)
+        ref = sum(int(w) for a, b, w in zip(g.i, g.j, g.w) if chi[a] != chi[b])
+        assert cuts[c] == ref and isinstance(cuts[c], int)
+    assert best == max(cuts) and cuts.index(best) == col
+
+
+def test_phase_retrieval_recovers_signal():
+    pd = W.phase_problem(64, 12, seed=0)
+    prob = PhaseProblem(pd.masks, pd.b)
+    res = sketchy_cgal(prob, R=5, T=300, seed=0)
+    chi = phase_round(res.U, res.Lam)
+    assert phase_error(chi, pd.chi) < 1e-2
+    assert res.history[-1]["infeas"] < 1e-2
+
+
+def test_stopping_rule_stops_at_tolerance():
+    g = W.cycle_graph(8)
+    prob = MaxCutProblem(g.n, g.i, g.j, g.w)
+    res = sketchy_cgal(prob, R=4, T=5000, seed=0, tol=1e-3)
+    assert res.converged_at is not None and res.converged_at < 5000
+    h = res.history[-1]
+    assert h["relgap"] <= 1e-3 and h["infeas"] <= 1e-3
+    assert res.t_done == res.converged_at - 1
+    # actual relative suboptimality of the implicit iterate is within tolerance
+    assert abs(h["p_orig"] - (-8.0)) / (1 + abs(h["p_orig"])) < 2e-3
+
+
+def test_trace_bounded_lmo_zero_direction():
+    """tr X <= alpha with xi >= 0 takes H = 0: z, S, p, tau shrink by (1 - eta)."""
+    pd = W.phase_problem(16, 12, seed=5)
+    prob = PhaseProblem(pd.masks, np.zeros_like(pd.b))   # b = 0: X = 0 is optimal
+    res = sketchy_cgal(prob, R=3, T=10, seed=0, trace_correct=False)
+    assert not any(h["h"] for h in res.history)
+    assert np.all(res.z == 0) and res.tau == 0.0 and res.p == 0.0
+    assert np.all(res.Lam == 0)
