@@ -1,0 +1,244 @@
+/*
+ * scgal.h -- C ABI of libscgal, a GB300 (sm_103a) SketchyCGAL solver for
+ * weakly constrained SDPs:
+ *
+ *     minimise <C, X>  subject to  A(X) = b,  X psd,  tr X = alpha  (or <= alpha)
+ *
+ * (Yurtsever, Tropp, Fercoq, Udell, Cevher, "Scalable Semidefinite
+ * Programming", arXiv 1912.02949: problem Eq. 1.4 / Eq. 2.2; the trace-bounded
+ * variant App. D.2).  The library touches the data only through the three
+ * primitives of Eq. 2.3 and keeps the O(d + R n) state of Alg. 6.1 (z, y, the
+ * Nystrom sketch S = X Omega) resident on the GPU.
+ *
+ * Conventions that hold for every call:
+ *  - Every function returns an int status (SCGAL_OK = 0, SCGAL_ENOTDONE = 1,
+ *    negative = error).  No C++ exception crosses this boundary.
+ *  - Array arguments may be host or device pointers (unified addressing);
+ *    the library copies what it keeps.  Inputs remain owned by the caller and
+ *    may be freed after the call returns.  Output buffers are caller-owned.
+ *  - A handle owns all its device state (CSR copy, Omega, S, Lanczos basis,
+ *    z, y) and one CUDA stream; calls on one handle must not overlap.
+ *  - After an error a handle is sticky-failed: later calls return the same
+ *    code until scgal_destroy.
+ *  - Quantities reported in scgal_stats are in the ORIGINAL units of the
+ *    problem even when the internal scaling of Eq. 7.1 is on.
+ */
+#ifndef SCGAL_H
+#define SCGAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scgal_ctx* scgal_t;        /* one SDP instance (opaque) */
+typedef struct scgal_server* scgal_srv_t; /* a serving loop (opaque) */
+
+enum scgal_status {
+    SCGAL_OK = 0,
+    SCGAL_ENOTDONE = 1,   /* iteration budget reached before the stopping rule */
+    SCGAL_EINVAL = -1,    /* bad argument or malformed input data */
+    SCGAL_ENOMEM = -2,    /* device allocation failed, or over the memory budget */
+    SCGAL_ECUDA = -3,     /* a CUDA runtime call failed */
+    SCGAL_ENUMERIC = -4,  /* non-finite value, or Nystrom factorisation failed */
+    SCGAL_ETIMEOUT = -5,  /* a poll or a device wait ran out of time */
+    SCGAL_EBUSY = -6,     /* server queue full */
+    SCGAL_ESTATE = -7     /* call not valid in the handle's current state */
+};
+
+enum { SCGAL_LMO_EQ = 0,   /* X in alpha * Delta_n: tr X = alpha (Alg. 6.1) */
+       SCGAL_LMO_LEQ = 1,  /* tr X <= alpha: H = 0 when xi >= 0 (App. D.2 item 1) */
+       SCGAL_LMO_DEFAULT = -1 };
+
+/* Solver parameters (Alg. 6.1 inputs R, T, beta0, K and the options of Section 7.1.2). */
+typedef struct {
+    int32_t  R;             /* sketch size, 1 <= R <= 32 (default 10) */
+    int32_t  T_max;         /* largest iteration index a solve may reach; sizes the
+                               stored Lanczos basis (q_T steps, Remark 4.2) (default 1000) */
+    double   tol;           /* stopping tolerance of Eq. E.1 on relative gap and
+                               infeasibility; <= 0 never stops early (default 0) */
+    double   beta0;         /* initial smoothing, beta_t = beta0 sqrt(t+1) (default 1) */
+    double   K;             /* dual bound; <= 0 or infinite means +inf (default +inf) */
+    int32_t  lmo;           /* SCGAL_LMO_*; DEFAULT = EQ for MaxCut, LEQ for phase */
+    int32_t  scale;         /* 1: scale the data as in Eq. 7.1 (default 1) */
+    int32_t  trace_correct; /* -1 default (on for EQ, off for LEQ), 0 off, 1 on (Alg. 6.1 last line) */
+    int32_t  precision;     /* 32: FP32 vectors/matvecs/sketch with FP64 reductions and
+                               dual state; 64: FP64 throughout (default 32) */
+    uint64_t seed;          /* seeds Omega and every Lanczos start vector */
+    uint32_t instance;      /* stream id of this instance's random draws (default 0) */
+    int32_t  check_every;   /* scgal_solve reads the stopping flag every k iterations (default 16) */
+} scgal_params;
+
+/* One iteration record (Alg. 6.1 step t; stopping values of Eq. E.1 for the
+ * state X_t before the update of step t). */
+typedef struct {
+    int64_t t;          /* iteration index */
+    int32_t q;          /* Lanczos steps requested, q_t = min(ceil(t^{1/4} ln n), n-1) */
+    int32_t k;          /* Lanczos steps completed (< q after breakdown) */
+    double  xi;         /* Ritz value lambda_min(T) of D_t (scaled problem) */
+    double  p;          /* <C, X_t> in original units */
+    double  relgap;     /* (p + <y,b> + beta/2 <z-b,z+b> - alpha xi) / (1 + |p|), original units */
+    double  infeas;     /* ||z - b|| / (1 + ||b||), original units */
+    double  gamma;      /* dual step size of Eq. 6.4 (0 if converged at t) */
+    int32_t converged;  /* 1 if X_t met the stopping rule (its update was not applied) */
+    int32_t reserved;
+} scgal_stats;
+
+/* Static description of a handle. */
+typedef struct {
+    int32_t n, d, R, precision, is_complex, lmo, trace_correct, scale;
+    int64_t nnz;          /* MaxCut: stored off-diagonal entries; phase: 0 */
+    int32_t weight_kind;  /* MaxCut: 0 unit, 1 +/-1 (sign packed in the column index), 2 general */
+    int32_t qmax;         /* Lanczos basis capacity */
+    int64_t t;            /* next iteration index (1 before the first step) */
+    double  alpha;        /* original alpha */
+    double  normC, normA; /* ||C||_F and ||A|| of the original data */
+    int64_t device_bytes; /* device memory held by the handle */
+    int32_t spmv_group;   /* lanes per CSR row chosen for the D-matvec */
+    int32_t reserved;
+} scgal_info;
+
+/* Fill *p with the defaults listed above. */
+void scgal_params_default(scgal_params* p);
+
+/* MaxCut SDP (Eq. 1.2) of an undirected weighted graph, as the instance
+ * C = -L/4, A = diag, b = 1 of Section 2.4 with L = sum_ij w_ij (e_i-e_j)(e_i-e_j)^T
+ * (Eq. 1.1 with weights).
+ *   row_ptr[n+1], col[nnz]: symmetric CSR of the adjacency, both directions of
+ *       every edge, no diagonal entries, 0 <= col < n, row_ptr[0] = 0,
+ *       row_ptr[n] = nnz, nondecreasing (checked: SCGAL_EINVAL).
+ *   w[nnz]: edge weights (finite), or NULL for unit weights.  If every weight
+ *       is +1 or -1 the signs are packed into the column indices (4 bytes per
+ *       stored entry).
+ *   alpha: trace bound; <= 0 selects alpha = n.
+ * On success *out is a new handle at t = 1 (z = y = 0, S = 0). */
+int scgal_create_maxcut(const int32_t* row_ptr, const int32_t* col, const double* w,
+                        int32_t n, int64_t nnz, double alpha,
+                        const scgal_params* params, scgal_t* out);
+
+/* Abstract phase retrieval SDP with coded diffraction patterns (Section 7.3,
+ * App. F.1): C = I, A_i = a_i a_i* with a_{j n + l}* x = (FFT(psi_j .* x))_l,
+ * unnormalised DFT, measurements b[j*n + l].
+ *   masks: L*n complex128 values as interleaved (re, im) doubles, mask-major;
+ *          every |psi_j[k]| must be 1 (the closed form ||A|| = n sqrt(L) of the
+ *          scaling needs it; checked: SCGAL_EINVAL).
+ *   L >= 1; n a power of two, 16 <= n <= 2^20.
+ *   b: L*n doubles.   alpha: <= 0 selects alpha = 3n (Section 7.3.3).
+ * The problem is complex Hermitian; vectors are complex64 (precision 32) or
+ * complex128 (precision 64). */
+int scgal_create_phase(const double* masks, int32_t L, int32_t n, const double* b, double alpha,
+                       const scgal_params* params, scgal_t* out);
+
+/* One SketchyCGAL iteration (Alg. 6.1 loop body): form D_t = C + A*(y + beta(z-b)),
+ * ApproxMinEvec (Alg. 4.1, stored basis), z / sketch / objective updates
+ * (Eq. 6.2), dual step (Eq. 6.3-6.4).  Blocks until done; *out (may be NULL)
+ * receives the record of this iteration.  Returns SCGAL_ESTATE if the handle
+ * already met its stopping rule or reached T_max. */
+int scgal_step(scgal_t h, scgal_stats* out);
+
+/* Iterate until the stopping rule (tol > 0) holds or iteration T has been
+ * done (T <= T_max).  Returns SCGAL_OK on convergence, SCGAL_ENOTDONE when T
+ * was reached first.  *out (may be NULL) receives the last record. */
+int scgal_solve(scgal_t h, int64_t T, scgal_stats* out);
+
+/* Nystrom reconstruction (Alg. B.1) of the implicit iterate, optional trace
+ * correction (Alg. 6.1 last line), in original units X = U diag(lambda) U*.
+ *   U[n*R]: column-major n x R (complex: interleaved re/im, 2*n*R doubles), or NULL
+ *   lambda[R]: descending eigenvalues, or NULL;  err[R]: Schatten-1 errors
+ *       err_r = tau - sum_{i<=r} lambda_i (Eq. B.4, before trace correction), or NULL
+ *   best_cut: MaxCut only -- weight of the best of the R cuts sgn(U) (Section 7.2.1;
+ *       sgn(0) = +1, ties to the lowest column); int64 exact for unit / +-1 weights,
+ *       rounded to nearest otherwise.  May be NULL.
+ * Returns SCGAL_ENUMERIC if the Cholesky factorisation fails at every shift. */
+int scgal_reconstruct(scgal_t h, double* U, double* lambda, double* err, int64_t* best_cut);
+
+/* Weight of the cut chi in {-1,+1}^n (int8, host or device) under the handle's
+ * graph: sum over edges of w_ij (1 - chi_i chi_j) / 2 (Section 7.2.1).  Exact
+ * int64 for unit / +-1 weights. */
+int scgal_cut_value(scgal_t h, const int8_t* chi, int64_t* cut);
+
+/* Apply the gradient operator of Eq. 6.1, out = D x with D = C' + A'*(w), to one
+ * vector in the handle's precision (the primitives (1) and (2) of Eq. 2.3 on the
+ * scaled data).  w[d] FP64 dual weights; NULL uses the handle's current
+ * w = y + beta_t (z - b).  x, out: n values (complex: 2n interleaved) as doubles,
+ * converted to and from the handle's precision. */
+int scgal_apply_D(scgal_t h, const double* w, const double* x, double* out);
+
+/* ApproxMinEvec (Alg. 4.1) on D = C' + A'*(w) with the random start vector of
+ * iteration t and q steps (q <= qmax).  w as in scgal_apply_D.  Outputs: *xi the
+ * Ritz value, *k steps done, v[n] (complex: 2n) the unit Ritz vector.  Does not
+ * change the solver state. */
+int scgal_lanczos(scgal_t h, const double* w, int64_t t, int32_t q, double* xi, int32_t* k,
+                  double* v);
+
+/* Read / overwrite the iteration state (checkpoint and resume; the random
+ * draws are keyed by (seed, t), so a resumed run continues bit for bit).
+ *   z[d], y[d]: scaled dual-side state; S[n*R] row-major (complex: 2*n*R
+ *   interleaved); scalars[4] = {p (scaled), tau (scaled), t, converged}.
+ * Any pointer may be NULL to skip that part (set_state keeps the old value). */
+int scgal_get_state(scgal_t h, double* z, double* y, double* S, double* scalars);
+int scgal_set_state(scgal_t h, const double* z, const double* y, const double* S,
+                    const double* scalars);
+
+/* Copy the records of iterations first .. first+count-1 (those still in the
+ * history ring of T_max entries). */
+int scgal_history(scgal_t h, int64_t first, int64_t count, scgal_stats* out);
+
+int scgal_get_info(scgal_t h, scgal_info* out);
+
+/* Use `stream` (a cudaStream_t) for all of the handle's work instead of its own. */
+int scgal_set_stream(scgal_t h, void* stream);
+
+int scgal_destroy(scgal_t h);
+
+const char* scgal_strerror(int status);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: a host loop that admits MaxCut requests as they arrive, keeps each
+ * admitted solve's state resident, runs admitted solves concurrently on the
+ * GPU (continuous batching: a request joins as soon as a slot and memory are
+ * free, while others are mid-solve) and reports per-request latency. */
+
+typedef struct {
+    int32_t  status;        /* SCGAL_OK converged, SCGAL_ENOTDONE hit T_max, < 0 error */
+    int32_t  n;
+    int64_t  iterations;    /* iterations whose update was applied */
+    double   relgap, infeas;
+    double   objective;     /* <C, X> original units (MaxCut: -SDP value estimate) */
+    int64_t  best_cut;      /* rounded cut weight (Section 7.2.1) */
+    double   lambda_max;    /* largest eigenvalue of the reconstruction */
+    double   queue_ms;      /* submit -> admission */
+    double   latency_ms;    /* submit -> result ready */
+} scgal_result;
+
+typedef struct {
+    int64_t submitted, admitted, completed, rejected;
+    int32_t active, queued;
+    int64_t device_bytes_in_use, device_bytes_peak;
+} scgal_server_stats;
+
+/* hbm_budget: bytes the server may hold on the device (admission control);
+ * max_slots: solves resident at once (1..256). */
+int scgal_server_create(size_t hbm_budget, int32_t max_slots, scgal_srv_t* out);
+
+/* Queue a MaxCut solve (arguments as scgal_create_maxcut; the data is copied
+ * before return).  params->tol and params->T_max bound the solve.  Non-blocking;
+ * *ticket identifies the request.  SCGAL_EBUSY if the queue is full. */
+int scgal_submit(scgal_srv_t s, const int32_t* row_ptr, const int32_t* col, const double* w,
+                 int32_t n, int64_t nnz, const scgal_params* params, uint64_t* ticket);
+
+/* Wait up to timeout_ms (0: just test, < 0: forever) for a request's result.
+ * SCGAL_ETIMEOUT if it is not ready; the result is kept until read once. */
+int scgal_poll(scgal_srv_t s, uint64_t ticket, scgal_result* out, int32_t timeout_ms);
+
+int scgal_server_get_stats(scgal_srv_t s, scgal_server_stats* out);
+
+/* Stops admitting, waits for running solves, frees everything. */
+int scgal_server_destroy(scgal_srv_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCGAL_H */

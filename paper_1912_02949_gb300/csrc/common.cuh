@@ -1,0 +1,182 @@
+// Device-side helpers shared by the libscgal kernels (sm_103a).
+//
+//  * Philox4x32-10 (Salmon et al., SC'11) and Box-Muller normals: the random
+//    draws of Alg. 4.1 (Lanczos start) and Alg. 5.1 (test matrix Omega).
+//    Stream convention: normal m of stream (seed, purpose, t, instance) is
+//    output (m & 1) of Box-Muller on Philox(counter = (m >> 1, t, purpose,
+//    instance), key = (seed lo, seed hi)); uniforms take 53 bits from output
+//    pairs (x0, x1) and (x2, x3).
+//  * Element traits for real (float, double) and complex (float2, double2)
+//    vectors: the Hermitian inner product Re(a* b), |a|^2, scaling.
+//  * A deterministic grid-wide reduction: each block writes its partial sums,
+//    the last block to arrive (atomic ticket, no spinning) adds the partials in
+//    a fixed order.  Results do not depend on block scheduling.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define SCGAL_BS 256          // threads per block of every reduction kernel
+#define SCGAL_RMAX 32         // largest sketch size R
+
+namespace scgal {
+
+// --------------------------------------------------------------------------
+// Philox4x32-10
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+enum { PURPOSE_OMEGA = 1, PURPOSE_LANCZOS = 2 };
+
+__device__ __forceinline__ uint4 philox_pair_bits(unsigned long long seed, unsigned purpose,
+                                                  unsigned t, unsigned inst, unsigned pair) {
+    return philox4x32_10(make_uint4(pair, t, purpose, inst),
+                         make_uint2((unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32)));
+}
+
+// Both normals of one pair, FP64 Box-Muller.
+__device__ __forceinline__ void normal_pair(unsigned long long seed, unsigned purpose, unsigned t,
+                                            unsigned inst, unsigned pair, double& n0, double& n1) {
+    const uint4 x = philox_pair_bits(seed, purpose, t, inst, pair);
+    const double u1 = ((double)(x.x >> 5) * 67108864.0 + (double)(x.y >> 6) + 0.5) * (1.0 / 9007199254740992.0);
+    const double u2 = ((double)(x.z >> 5) * 67108864.0 + (double)(x.w >> 6) + 0.5) * (1.0 / 9007199254740992.0);
+    const double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    n0 = r * c;
+    n1 = r * s;
+}
+
+// Same pair evaluated in FP32 (the mixed-precision path draws its per-iteration
+// Lanczos start this way; the 53-bit uniform is rounded to FP32 first).
+__device__ __forceinline__ void normal_pair(unsigned long long seed, unsigned purpose, unsigned t,
+                                            unsigned inst, unsigned pair, float& n0, float& n1) {
+    const uint4 x = philox_pair_bits(seed, purpose, t, inst, pair);
+    const float u1 = fmaf((float)(x.x >> 5), 67108864.0f, (float)(x.y >> 6) + 0.5f) * 1.1102230246251565e-16f;
+    const float u2 = fmaf((float)(x.z >> 5), 67108864.0f, (float)(x.w >> 6) + 0.5f) * 1.1102230246251565e-16f;
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    n0 = r * c;
+    n1 = r * s;
+}
+
+// --------------------------------------------------------------------------
+// Element traits
+template <typename V> struct VT;
+// R: real scalar type; D: the FP64 element type of the same field.
+template <> struct VT<float>   { typedef float  R; typedef double  D; static constexpr bool cplx = false; };
+template <> struct VT<double>  { typedef double R; typedef double  D; static constexpr bool cplx = false; };
+template <> struct VT<float2>  { typedef float  R; typedef double2 D; static constexpr bool cplx = true; };
+template <> struct VT<double2> { typedef double R; typedef double2 D; static constexpr bool cplx = true; };
+
+__device__ __forceinline__ float  dotre(float a, float b) { return a * b; }
+__device__ __forceinline__ double dotre(double a, double b) { return a * b; }
+__device__ __forceinline__ float  dotre(float2 a, float2 b) { return a.x * b.x + a.y * b.y; }
+__device__ __forceinline__ double dotre(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
+__device__ __forceinline__ float  abs2(float a) { return a * a; }
+__device__ __forceinline__ double abs2(double a) { return a * a; }
+__device__ __forceinline__ float  abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double abs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+__device__ __forceinline__ float  vscale(float a, float s) { return a * s; }
+__device__ __forceinline__ double vscale(double a, double s) { return a * s; }
+__device__ __forceinline__ float2 vscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 vscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// a*x + b*y + c*z with real coefficients
+__device__ __forceinline__ float  lin3(float a, float x, float b, float y, float c, float z) { return fmaf(a, x, fmaf(b, y, c * z)); }
+__device__ __forceinline__ double lin3(double a, double x, double b, double y, double c, double z) { return fma(a, x, fma(b, y, c * z)); }
+__device__ __forceinline__ float2 lin3(float a, float2 x, float b, float2 y, float c, float2 z) {
+    return make_float2(fmaf(a, x.x, fmaf(b, y.x, c * z.x)), fmaf(a, x.y, fmaf(b, y.y, c * z.y)));
+}
+__device__ __forceinline__ double2 lin3(double a, double2 x, double b, double2 y, double c, double2 z) {
+    return make_double2(fma(a, x.x, fma(b, y.x, c * z.x)), fma(a, x.y, fma(b, y.y, c * z.y)));
+}
+// acc += a * x (real coefficient)
+__device__ __forceinline__ void vaxpy(float& acc, float a, float x) { acc = fmaf(a, x, acc); }
+__device__ __forceinline__ void vaxpy(double& acc, double a, double x) { acc = fma(a, x, acc); }
+__device__ __forceinline__ void vaxpy(float2& acc, float a, float2 x) { acc.x = fmaf(a, x.x, acc.x); acc.y = fmaf(a, x.y, acc.y); }
+__device__ __forceinline__ void vaxpy(double2& acc, double a, double2 x) { acc.x = fma(a, x.x, acc.x); acc.y = fma(a, x.y, acc.y); }
+
+template <typename V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ float vzero<float>() { return 0.f; }
+template <> __device__ __forceinline__ double vzero<double>() { return 0.0; }
+template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
+
+__device__ __forceinline__ void from_f64(float& o, double a) { o = (float)a; }
+__device__ __forceinline__ void from_f64(double& o, double a) { o = a; }
+
+// --------------------------------------------------------------------------
+// Deterministic grid reduction of NV doubles (blockDim.x == SCGAL_BS; 1-D or
+// 2-D grids, blocks numbered blockIdx.y * gridDim.x + blockIdx.x).
+// Returns true in exactly one block (the last to arrive); there tot[0..NV)
+// (shared memory) holds the grid totals for every thread after the call.
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* __restrict__ partials,
+                                            unsigned* __restrict__ ticket, double* tot) {
+    __shared__ double red[SCGAL_BS / 32][NV];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned nblk = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[wid][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < SCGAL_BS / 32; ++w) s += red[w][threadIdx.x];
+        partials[(size_t)threadIdx.x * nblk + bid] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(ticket, 1u);
+        last = (prev == nblk - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    // fixed-order sum of the partials
+    for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+        for (unsigned b = threadIdx.x; b < nblk; b += SCGAL_BS) s += __ldcg(&partials[(size_t)k * nblk + b]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) red[wid][0] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int w = 0; w < SCGAL_BS / 32; ++w) t += red[w][0];
+            tot[k] = t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    __syncthreads();
+    return true;
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_reduce_2d(double (&v)[NV], double* __restrict__ partials,
+                                               unsigned* __restrict__ ticket, double* tot) {
+    return grid_reduce<NV>(v, partials, ticket, tot);
+}
+
+}  // namespace scgal

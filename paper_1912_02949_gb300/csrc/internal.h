@@ -1,0 +1,190 @@
+// Internal declarations of libscgal: the device-resident iteration scalars,
+// the kernel parameter block, the handle, and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "scgal.h"
+#include "common.cuh"
+
+namespace scgal {
+
+enum ProblemKind { KIND_MAXCUT = 0, KIND_PHASE = 1 };
+enum WeightKind { W_UNIT = 0, W_PM1 = 1, W_REAL = 2 };
+
+// Scalars of the current iteration, resident in device memory so that a
+// captured iteration graph can be replayed for every t with the same q.
+struct DevScalars {
+    long long t;        // iteration being executed (set by the dual/start kernel)
+    int k;              // Lanczos steps completed
+    int stop;           // Lanczos breakdown flag (rho_i == 0)
+    int converged;      // stopping rule met at iteration conv_t
+    int err;            // sticky device error (SCGAL_ENUMERIC)
+    long long conv_t;
+    int take_h;         // 0: trace-bounded LMO chose H = 0
+    int pad;
+    double beta, eta;   // beta_t, eta_t
+    double xi;          // Ritz value of iteration t
+    double nv2;         // ||v||^2 of the unnormalised Ritz vector
+    double vCv;         // v* C v (unnormalised v)
+    double p, tau;      // <C', X'>, tr X' (scaled)
+    double yb, zbzpb, nzb2;   // <y,b>, <z-b, z+b>, ||z-b||^2 of the state before the update
+    double nzb2_new, yzb_new, yy; // after the z update: ||z-b||^2, <y, z-b>, ||y||^2
+    double gamma;
+    double r[2 * SCGAL_RMAX];   // Omega* v (re, im) of the unnormalised Ritz vector
+};
+
+// Problem constants of the scaled instance (Eq. 7.1) and the solver options.
+struct Consts {
+    int kind;           // ProblemKind
+    int n, d, R, L;
+    long long nnz;
+    int wkind;
+    int lmo;            // SCGAL_LMO_EQ / LEQ
+    int b_const;        // MaxCut: b' is the constant bconst
+    int K_finite;
+    double sC, sA;      // C' = sC C, A' = sA A
+    double coff;        // off-diagonal coefficient of C' (MaxCut: sC / 4)
+    double alpha;       // alpha of the scaled problem
+    double bconst;
+    double beta0, K, tol;
+    double obj_factor, z_factor, normb_orig, normA_s;
+    unsigned long long seed;
+    unsigned instance;
+    int hist_cap;
+    int qmax;           // Lanczos basis capacity (steps)
+};
+
+// Pointers of one handle, passed by value to every kernel.
+template <typename V>
+struct KP {
+    Consts c;
+    // MaxCut data
+    const int* row_ptr;
+    const int* col;     // sign of the weight in bit 31 when wkind == W_PM1
+    const typename VT<V>::R* val;    // wkind == W_REAL only
+    const typename VT<V>::R* cdiag;  // diagonal of C'
+    typename VT<V>::R* dvec;         // diagonal of D = C' + A'*(w) (MaxCut)
+    // phase retrieval data
+    const V* masks;     // L x n
+    typename VT<V>::R* wvec;         // sA * (y + beta (z - b)), d entries (phase retrieval)
+    V* fftbuf;          // L x n scratch for the four-step FFT passes
+    const V* twiddle;   // n roots of unity exp(-2 pi i k / n)
+    int log2n, n1, n2;  // n = n1 * n2 (four-step split)
+    int log1, log2;     // log2 n1, log2 n2
+    int ph_tc;          // columns per block in the column passes
+    int ph_rpb;         // rows per block in the row pass
+    int ph_mb;          // masks per block in the last pass (ynplanes = ceil(L / ph_mb))
+    int ynplanes;       // planes of ybuf summed to form D x (1 for MaxCut)
+    // state
+    double* z;
+    double* y;
+    const double* b;
+    V* basis;           // (qmax + 1) x ldb raw Lanczos vectors
+    long long ldb;
+    V* ybuf;            // D x of the current Lanczos step (ynplanes partial planes, stride ldb)
+    V* vbuf;            // unnormalised Ritz vector
+    const V* Omega;     // n x R row-major
+    V* S;               // n x R row-major
+    // reductions and scalars
+    double* partials;
+    unsigned* ticket;
+    DevScalars* sc;
+    double* om;         // omega_i
+    double* rh;         // rho_i
+    double* sv;         // 1 / ||w_i|| of raw basis vector i
+    double* coef;       // Ritz coefficients u_j * sv_j
+    scgal_stats* hist;
+};
+
+}  // namespace scgal
+
+// ---------------------------------------------------------------------------
+struct scgal_ctx {
+    int kind = 0;
+    int prec = 32;
+    int cplx = 0;
+    scgal_params prm{};
+    scgal::Consts c{};
+    int n = 0, d = 0, R = 0, L = 0;
+    long long nnz = 0;
+    int qmax = 0;
+    long long ldb = 0;
+    double alpha_orig = 0, normC = 0, normA = 0;
+    int trace_correct = 1;
+    int spmv_group = 8;
+    int grid_elem = 1, grid_spmv = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sticky = 0;
+    long long t_next = 1;       // host view of the next iteration index
+    int device = 0;
+    // device allocations (one list, freed on destroy)
+    std::vector<void*> allocs;
+    long long device_bytes = 0;
+    void* kp = nullptr;         // scgal::KP<V> (host copy), typed by precision/kind
+    std::map<int, cudaGraphExec_t> graphs;
+    std::string last_error;
+    int converged_host = 0;     // the stopping rule held at iteration t_next
+    int* flag_host = nullptr;   // pinned copy of the device convergence flag
+    cudaEvent_t flag_event = nullptr;
+    // reconstruction work space (allocated on first use)
+    void* rec_part = nullptr;
+    void* rec_Y = nullptr;
+    void* rec_U = nullptr;
+    double* rec_small = nullptr;
+    void* rec_cut = nullptr;
+    void* aux = nullptr;        // scratch of the single-primitive entry points
+    // phase retrieval
+    void* phase_extra = nullptr;
+};
+
+namespace scgal {
+
+int ctx_alloc(scgal_ctx* h, void** p, size_t bytes);
+int launch_iterations(scgal_ctx* h, long long T_end);
+int finish_iterations(scgal_ctx* h, scgal_stats* out, int* converged);
+
+// launchers (templated on the vector element type V; explicit instantiations
+// for float/double (MaxCut) and float2/double2 (phase retrieval))
+template <typename V> void launch_dual_start(const KP<V>& p, int grid, int do_dual, cudaStream_t s);
+template <typename V> void launch_lanczos_update(const KP<V>& p, int grid, int i, cudaStream_t s);
+template <typename V> void launch_tridiag(const KP<V>& p, int q, cudaStream_t s);
+template <typename V> void launch_ritz(const KP<V>& p, int grid, cudaStream_t s);
+template <typename V> void launch_gen_omega(const KP<V>& p, int grid, cudaStream_t s);
+template <typename V> void launch_start_only(const KP<V>& p, int grid, long long t, cudaStream_t s);
+
+// creation, rounding and reconstruction helpers
+int maxcut_check_and_scan(const int* row_ptr, const int* col, const double* w, int n, long long nnz, int* flags,
+                          double* deg, double* partials, unsigned* ticket, double* out2, int grid, cudaStream_t s);
+template <typename R>
+void maxcut_pack(const int* col_in, const double* w, long long nnz, int wkind, int* col_out, R* val_out,
+                 const double* deg, double sC, int n, R* cdiag, int grid, cudaStream_t s);
+template <typename R>
+void maxcut_cut(const int* row_ptr, const int* col, const R* val, int wkind, int n, const double* U, long long ldu,
+                const signed char* chi, int ncols, unsigned long long* icut, double* fcut, int grid, cudaStream_t s);
+void phase_perm(const double* in, double* out, long long d, int n, int n1, int n2, int to_internal, cudaStream_t s);
+template <typename V>
+int nystrom_reconstruct(const V* S, const V* Om, int n, int R, double tau, int trace_correct, double alpha,
+                        double2* part, int grid, double2* G, double2* L, double2* M, double* scal,
+                        typename VT<V>::D* Y, typename VT<V>::D* U, double* lam, double* err, cudaStream_t s);
+
+// MaxCut
+template <typename V> void launch_spmv_step(const KP<V>& p, int grid, int group, int i, cudaStream_t s);
+template <typename V> void launch_vcv_update(const KP<V>& p, int grid, int group, cudaStream_t s);
+template <typename V> void launch_apply_D_maxcut(const KP<V>& p, int grid, int group, const V* x, V* out,
+                                                 const V* diag, cudaStream_t s);
+template <typename V> void launch_dvec_from_w(const KP<V>& p, int grid, const double* w, cudaStream_t s);
+
+// Phase retrieval
+template <typename V> void launch_phase_step(const KP<V>& p, int i, cudaStream_t s);
+template <typename V> void launch_phase_update(const KP<V>& p, int grid, cudaStream_t s);
+template <typename V> void launch_apply_D_phase(const KP<V>& p, const V* x, V* out, const typename VT<V>::R* w, cudaStream_t s);
+template <typename V> void launch_wvec_from_w(const KP<V>& p, int grid, const double* w, cudaStream_t s);
+
+}  // namespace scgal

@@ -1,0 +1,360 @@
+// Coded-diffraction phase retrieval operators (Section 7.3, App. F.1).
+//
+//   D u = sC u + sum_j conj(psi_j) .* W*( w_j .* W(psi_j .* u) )     (primitives (1)+(2))
+//   A(v v*)_j = |W(psi_j .* v)|^2                                     (primitive (3))
+// with W the unnormalised n-point DFT (n = 2^m), W* its adjoint, and
+// w_j = sA (y + beta (z - b))_j.  Every transform is a four-step FFT with
+// n = n1 * n2 (input index k = k1 + n1 k2, output l = l2 + n2 l1):
+//   P1 (columns k1):  length-n2 DFT over k2 of psi_j .* u, times exp(-2 pi i k1 l2 / n)
+//   P2 (rows l2):     length-n1 DFT over k1 -> W(psi_j u) at l = l2 + n2 l1,
+//                     times w_j, inverse length-n1 DFT, times exp(+2 pi i l2 m1 / n)
+//   P3 (columns m1):  inverse length-n2 DFT over l2 -> W*(...) at m = m1 + n1 m2,
+//                     times conj(psi_j), summed over the masks of the block's group.
+// Each block keeps its transforms in shared memory (radix-2, bit-reversed
+// loads); the d-indexed vectors z, y, b, w are stored in the order the P2 rows
+// produce them, internal index j n + l2 n1 + l1 for measurement (j, l2 + n2 l1),
+// so P2 reads and writes them contiguously.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace scgal {
+
+template <typename V> struct CX;
+template <> struct CX<float2> {
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+    static __device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }  // conj(a) b
+};
+template <> struct CX<double2> {
+    static __device__ __forceinline__ double2 mul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+    static __device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
+};
+
+__device__ __forceinline__ int brev(int i, int bits) { return (int)(__brev((unsigned)i) >> (32 - bits)); }
+
+// exp(sign * 2 pi i k / n) from the table of exp(-2 pi i k / n)
+template <typename V>
+__device__ __forceinline__ V twid(const V* tw, int k, int n, int sign) {
+    V w = tw[k & (n - 1)];
+    if (sign > 0) w.y = -w.y;
+    return w;
+}
+
+// In-place radix-2 DIT FFTs on `batch` sequences of length 2^lg held in shared
+// memory with element stride es and batch stride bs; input in bit-reversed order.
+template <typename V>
+__device__ void smem_fft(V* x, int lg, int batch, int es, int bs, const V* tw, int n, int sign) {
+    const int len = 1 << lg;
+    const int half_total = (len >> 1) * batch;
+    for (int s = 1; s <= lg; ++s) {
+        const int half = 1 << (s - 1);
+        const int tstride = n >> s;   // twiddle exp(sign 2 pi i pos / 2^s) = tw[pos * n / 2^s]
+        for (int idx = threadIdx.x; idx < half_total; idx += blockDim.x) {
+            const int b = idx / (len >> 1);
+            const int k = idx - b * (len >> 1);
+            const int grp = k >> (s - 1);
+            const int pos = k & (half - 1);
+            const int i0 = grp * 2 * half + pos;
+            const int i1 = i0 + half;
+            V* a0 = x + b * bs + i0 * es;
+            V* a1 = x + b * bs + i1 * es;
+            const V w = twid(tw, pos * tstride, n, sign);
+            const V u = *a0;
+            const V t = CX<V>::mul(*a1, w);
+            a0->x = u.x + t.x;
+            a0->y = u.y + t.y;
+            a1->x = u.x - t.x;
+            a1->y = u.y - t.y;
+        }
+        __syncthreads();
+    }
+}
+
+// P1: columns [cb*TC, cb*TC+TC) of mask j = blockIdx.y.
+template <typename V>
+__global__ void __launch_bounds__(SCGAL_BS) k_ph_p1(KP<V> p, const V* __restrict__ x) {
+    extern __shared__ unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    const int n = p.c.n, n1 = p.n1, n2 = p.n2, TC = p.ph_tc, lg2 = p.log2;
+    const int j = blockIdx.y;
+    const int k1base = blockIdx.x * TC;
+    const V* __restrict__ mask = p.masks + (size_t)j * n;
+    for (int idx = threadIdx.x; idx < n2 * TC; idx += blockDim.x) {
+        const int k2 = idx / TC, c = idx - k2 * TC;
+        const int e = k1base + c + n1 * k2;
+        sm[brev(k2, lg2) * TC + c] = CX<V>::mul(x[e], mask[e]);
+    }
+    __syncthreads();
+    smem_fft<V>(sm, lg2, TC, TC, 1, p.twiddle, n, -1);
+    V* out = p.fftbuf + (size_t)j * n;
+    for (int idx = threadIdx.x; idx < n2 * TC; idx += blockDim.x) {
+        const int l2 = idx / TC, c = idx - l2 * TC;
+        const int k1 = k1base + c;
+        out[(size_t)l2 * n1 + k1] = CX<V>::mul(sm[l2 * TC + c], twid(p.twiddle, k1 * l2, n, -1));
+    }
+}
+
+// P2 mode 0: forward row DFT, times w, inverse row DFT, inverse twiddle.
+// P2 mode 1: forward row DFT and the primal update z <- (1-eta) z + zc |X|^2,
+//            with the partial sums for the dual step (fused with the S update).
+template <typename V, int MODE>
+__global__ void __launch_bounds__(SCGAL_BS) k_ph_p2(KP<V> p, const typename VT<V>::R* __restrict__ w) {
+    typedef typename VT<V>::R Rt;
+    extern __shared__ unsigned char smraw[];
+    if (MODE == 1 && p.sc->converged) return;
+    const int n = p.c.n, n1 = p.n1, RPB = p.ph_rpb, lg1 = p.log1;
+    V* sa = reinterpret_cast<V*>(smraw);
+    V* sb = sa + RPB * n1;
+    const int j = blockIdx.y;
+    const int l2base = blockIdx.x * RPB;
+    V* buf = p.fftbuf + (size_t)j * n + (size_t)l2base * n1;
+    for (int idx = threadIdx.x; idx < RPB * n1; idx += blockDim.x) {
+        const int r = idx / n1, k1 = idx - r * n1;
+        sa[r * n1 + brev(k1, lg1)] = buf[idx];
+    }
+    __syncthreads();
+    smem_fft<V>(sa, lg1, RPB, 1, n1, p.twiddle, n, -1);
+    if constexpr (MODE == 0) {
+        const Rt* wj = w + (size_t)j * n + (size_t)l2base * n1;
+        for (int idx = threadIdx.x; idx < RPB * n1; idx += blockDim.x) {
+            const int r = idx / n1, l1 = idx - r * n1;
+            const Rt ww = wj[idx];
+            V v = sa[idx];
+            v.x *= ww;
+            v.y *= ww;
+            sb[r * n1 + brev(l1, lg1)] = v;
+        }
+        __syncthreads();
+        smem_fft<V>(sb, lg1, RPB, 1, n1, p.twiddle, n, +1);
+        for (int idx = threadIdx.x; idx < RPB * n1; idx += blockDim.x) {
+            const int r = idx / n1, m1 = idx - r * n1;
+            buf[idx] = CX<V>::mul(sb[idx], twid(p.twiddle, (l2base + r) * m1, n, +1));
+        }
+    } else {
+        DevScalars* sc = p.sc;
+        const double eta = sc->eta, nv2 = sc->nv2;
+        const int take = sc->take_h;
+        const double zc = take ? eta * p.c.alpha * p.c.sA / nv2 : 0.0;
+        double a_nzb = 0.0, a_yzb = 0.0, a_yy = 0.0;
+        const size_t base = (size_t)j * n + (size_t)l2base * n1;
+        for (int idx = threadIdx.x; idx < RPB * n1; idx += blockDim.x) {
+            const size_t i = base + idx;
+            const V X = sa[idx];
+            const double a2 = (double)X.x * X.x + (double)X.y * X.y;
+            const double zi = fma(1.0 - eta, p.z[i], zc * a2);
+            p.z[i] = zi;
+            const double zb = zi - p.b[i];
+            a_nzb = fma(zb, zb, a_nzb);
+            if (p.c.K_finite) {
+                const double yi = p.y[i];
+                a_yzb = fma(yi, zb, a_yzb);
+                a_yy = fma(yi, yi, a_yy);
+            }
+        }
+        // sketch update S <- (1-eta) S + eta alpha v (v* Omega) / ||v||^2 (grid-stride over n R)
+        const int R = p.c.R;
+        __shared__ V rr[SCGAL_RMAX];
+        if (threadIdx.x < R) {
+            rr[threadIdx.x].x = (Rt)sc->r[2 * threadIdx.x];
+            rr[threadIdx.x].y = (Rt)sc->r[2 * threadIdx.x + 1];
+        }
+        __syncthreads();
+        const Rt sfac = take ? (Rt)(eta * p.c.alpha / nv2) : (Rt)0;
+        const Rt om1 = (Rt)(1.0 - eta);
+        const long long nR = (long long)n * R;
+        const long long gt = (long long)(blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+        const long long st = (long long)gridDim.x * gridDim.y * blockDim.x;
+        for (long long k = gt; k < nR; k += st) {
+            const int e = (int)(k / R);
+            const int c = (int)(k - (long long)e * R);
+            const V vr = CX<V>::mul(p.vbuf[e], rr[c]);
+            V s = p.S[k];
+            s.x = om1 * s.x + sfac * vr.x;
+            s.y = om1 * s.y + sfac * vr.y;
+            p.S[k] = s;
+        }
+        double red[3] = {a_nzb, a_yzb, a_yy};
+        __shared__ double tot[3];
+        if (grid_reduce_2d<3>(red, p.partials, p.ticket, tot)) {
+            if (threadIdx.x == 0) {
+                const Consts& c = p.c;
+                sc->vCv = c.sC;
+                sc->p = (1.0 - eta) * sc->p + (take ? eta * c.alpha * c.sC : 0.0);
+                sc->tau = (1.0 - eta) * sc->tau + (take ? eta * c.alpha : 0.0);
+                const double nzb2 = tot[0];
+                const long long t = sc->t;
+                double gamma = (nzb2 == 0.0)
+                                   ? c.beta0
+                                   : fmin(c.beta0, 4.0 * c.alpha * c.alpha * c.beta0 * c.normA_s * c.normA_s /
+                                                       (pow((double)(t + 1), 1.5) * nzb2));
+                if (c.K_finite) {
+                    const double yy = tot[2] + 2.0 * gamma * tot[1] + gamma * gamma * nzb2;
+                    if (sqrt(yy) > c.K) gamma = 0.0;
+                }
+                sc->gamma = gamma;
+                sc->nzb2_new = nzb2;
+                p.hist[(t - 1) % c.hist_cap].gamma = gamma;
+            }
+        }
+    }
+}
+
+// P3: columns [cb*TC, ...) and the masks of group g = blockIdx.y; writes plane g
+// of the output.  DOT: also reduce Re<x, D x> for the Lanczos step i.
+template <typename V, int DOT>
+__global__ void __launch_bounds__(SCGAL_BS) k_ph_p3(KP<V> p, const V* __restrict__ x, V* __restrict__ out, int i) {
+    typedef typename VT<V>::R Rt;
+    constexpr int MAXE = 16;   // elements per thread (n2 * TC <= 16 * SCGAL_BS)
+    extern __shared__ unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    DevScalars* sc = p.sc;
+    if (DOT && (sc->converged || sc->stop)) return;
+    const int n = p.c.n, n1 = p.n1, n2 = p.n2, TC = p.ph_tc, lg2 = p.log2, L = p.c.L;
+    const int m1base = blockIdx.x * TC;
+    const int g = blockIdx.y;
+    const int j0 = g * p.ph_mb, j1 = min(L, j0 + p.ph_mb);
+    V acc[MAXE];
+#pragma unroll
+    for (int s = 0; s < MAXE; ++s) acc[s] = vzero<V>();
+    const int nel = n2 * TC;
+    for (int j = j0; j < j1; ++j) {
+        const V* buf = p.fftbuf + (size_t)j * n;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+            const int l2 = idx / TC, c = idx - l2 * TC;
+            sm[brev(l2, lg2) * TC + c] = buf[(size_t)l2 * n1 + m1base + c];
+        }
+        __syncthreads();
+        smem_fft<V>(sm, lg2, TC, TC, 1, p.twiddle, n, +1);
+        const V* mask = p.masks + (size_t)j * n;
+#pragma unroll
+        for (int s = 0; s < MAXE; ++s) {
+            const int idx = threadIdx.x + s * SCGAL_BS;
+            if (idx < nel) {
+                const int m2 = idx / TC, c = idx - m2 * TC;
+                const int e = m1base + c + n1 * m2;
+                const V hcon = CX<V>::cmul(mask[e], sm[idx]);   // conj(psi) * H
+                acc[s].x += hcon.x;
+                acc[s].y += hcon.y;
+            }
+        }
+    }
+    Rt dot = 0;
+    const Rt sC = (Rt)p.c.sC;
+#pragma unroll
+    for (int s = 0; s < MAXE; ++s) {
+        const int idx = threadIdx.x + s * SCGAL_BS;
+        if (idx < nel) {
+            const int m2 = idx / TC, c = idx - m2 * TC;
+            const int e = m1base + c + n1 * m2;
+            V val = acc[s];
+            const V xe = x[e];
+            if (g == 0) {
+                val.x += sC * xe.x;
+                val.y += sC * xe.y;
+            }
+            out[(size_t)g * p.ldb + e] = val;
+            if (DOT) dot += xe.x * val.x + xe.y * val.y;
+        }
+    }
+    if constexpr (DOT) {
+        double v[1] = {(double)dot};
+        __shared__ double tot[1];
+        if (grid_reduce_2d<1>(v, p.partials, p.ticket, tot)) {
+            if (threadIdx.x == 0) {
+                const double si = p.sv[i];
+                const double om = si * si * tot[0];
+                if (!isfinite(om)) {
+                    sc->err = SCGAL_ENUMERIC;
+                    sc->converged = 1;
+                }
+                p.om[i] = om;
+                sc->k = i + 1;
+            }
+        }
+    }
+}
+
+template <typename V>
+__global__ void k_plane_sum(const V* planes, int np, long long ldb, int n, V* out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        V s = planes[e];
+        for (int g = 1; g < np; ++g) {
+            s.x += planes[(size_t)g * ldb + e].x;
+            s.y += planes[(size_t)g * ldb + e].y;
+        }
+        out[e] = s;
+    }
+}
+
+// w (FP64, natural measurement order) -> sA w in the internal order.
+template <typename V>
+__global__ void k_wvec_from_w(KP<V> p, const double* w) {
+    typedef typename VT<V>::R Rt;
+    const int n = p.c.n, n1 = p.n1, n2 = p.n2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.c.d; i += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(i / n);
+        const int l = (int)(i - (long long)j * n);
+        const int l2 = l % n2, l1 = l / n2;
+        p.wvec[(size_t)j * n + (size_t)l2 * n1 + l1] = (Rt)(p.c.sA * w[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <typename V> static size_t col_smem(const KP<V>& p) { return sizeof(V) * (size_t)p.n2 * p.ph_tc; }
+template <typename V> static size_t row_smem(const KP<V>& p) { return 2 * sizeof(V) * (size_t)p.n1 * p.ph_rpb; }
+
+template <typename V>
+static void forward_and_weight(const KP<V>& p, const V* x, const typename VT<V>::R* w, cudaStream_t s) {
+    k_ph_p1<V><<<dim3(p.n1 / p.ph_tc, p.c.L), SCGAL_BS, col_smem(p), s>>>(p, x);
+    k_ph_p2<V, 0><<<dim3(p.n2 / p.ph_rpb, p.c.L), SCGAL_BS, row_smem(p), s>>>(p, w);
+}
+
+template <typename V> void launch_phase_step(const KP<V>& p, int i, cudaStream_t s) {
+    const V* x = p.basis + (size_t)i * p.ldb;
+    // the column and row passes skip nothing on breakdown; only their cost is wasted
+    forward_and_weight<V>(p, x, p.wvec, s);
+    k_ph_p3<V, 1><<<dim3(p.n1 / p.ph_tc, p.ynplanes), SCGAL_BS, col_smem(p), s>>>(p, x, p.ybuf, i);
+}
+
+template <typename V> void launch_phase_update(const KP<V>& p, int grid, cudaStream_t s) {
+    (void)grid;
+    k_ph_p1<V><<<dim3(p.n1 / p.ph_tc, p.c.L), SCGAL_BS, col_smem(p), s>>>(p, p.vbuf);
+    k_ph_p2<V, 1><<<dim3(p.n2 / p.ph_rpb, p.c.L), SCGAL_BS, row_smem(p), s>>>(p, nullptr);
+}
+
+template <typename V>
+void launch_apply_D_phase(const KP<V>& p, const V* x, V* out, const typename VT<V>::R* w, cudaStream_t s) {
+    forward_and_weight<V>(p, x, w, s);
+    k_ph_p3<V, 0><<<dim3(p.n1 / p.ph_tc, p.ynplanes), SCGAL_BS, col_smem(p), s>>>(p, x, p.ybuf, 0);
+    k_plane_sum<V><<<(p.c.n + 255) / 256, 256, 0, s>>>(p.ybuf, p.ynplanes, p.ldb, p.c.n, out);
+}
+
+template <typename V> void launch_wvec_from_w(const KP<V>& p, int grid, const double* w, cudaStream_t s) {
+    k_wvec_from_w<V><<<grid, SCGAL_BS, 0, s>>>(p, w);
+}
+
+// natural measurement order (j n + l2 + n2 l1) <-> internal order (j n + l2 n1 + l1)
+__global__ void k_phase_perm(const double* in, double* out, long long d, int n, int n1, int n2, int to_internal) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d; i += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(i / n);
+        const int l = (int)(i - (long long)j * n);
+        const long long k = (long long)j * n + (long long)(l % n2) * n1 + l / n2;
+        if (to_internal) out[k] = in[i];
+        else out[i] = in[k];
+    }
+}
+void phase_perm(const double* in, double* out, long long d, int n, int n1, int n2, int to_internal, cudaStream_t s) {
+    k_phase_perm<<<(int)std::min<long long>((d + 255) / 256, 4096), 256, 0, s>>>(in, out, d, n, n1, n2, to_internal);
+}
+
+#define INST(V)                                                                                           \
+    template void launch_phase_step<V>(const KP<V>&, int, cudaStream_t);                                  \
+    template void launch_phase_update<V>(const KP<V>&, int, cudaStream_t);                                \
+    template void launch_apply_D_phase<V>(const KP<V>&, const V*, V*, const typename VT<V>::R*, cudaStream_t); \
+    template void launch_wvec_from_w<V>(const KP<V>&, int, const double*, cudaStream_t);
+INST(float2)
+INST(double2)
+#undef INST
+
+}  // namespace scgal

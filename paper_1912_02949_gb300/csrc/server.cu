@@ -1,0 +1,298 @@
+// Serving loop of libscgal: continuous batching of MaxCut SDP solves.
+//
+// A worker thread owns up to max_slots resident solves.  Each round it
+//   1. admits queued requests, oldest first, while a slot is free and the
+//      request's estimated device footprint fits the remaining budget (the
+//      solve's z, y, sketch and Lanczos basis then stay on the device until it
+//      finishes);
+//   2. enqueues the next chunk of iterations of every resident solve, each on
+//      the solve's own stream, before waiting for any of them, so the solves'
+//      kernels overlap on the GPU;
+//   3. retires the solves that met their stopping rule (Eq. E.1) or their
+//      T_max: Nystrom reconstruction, rounding, result published for scgal_poll.
+// A request that arrives while others are mid-solve joins at the next round.
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+    uint64_t id = 0;
+    std::vector<int32_t> row_ptr, col;
+    std::vector<double> w;
+    bool has_w = false;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    scgal_params prm{};
+    double t_submit = 0, t_admit = 0;
+    size_t footprint = 0;
+};
+
+struct Slot {
+    scgal_t h = nullptr;
+    Request req;
+    bool active = false;
+};
+
+// Device bytes of one FP32 solve (mirrors the handle's allocations, with margin).
+size_t estimate_footprint(int n, long long nnz, const scgal_params& p) {
+    const double q = std::ceil(std::pow((double)p.T_max, 0.25) * std::log((double)n));
+    const double qmax = std::min<double>(q, n - 1);
+    const double ldb = (double)((n + 63) / 64 * 64);
+    const double vb = p.precision == 64 ? 8.0 : 4.0;
+    double bytes = 4.0 * (n + 1) + 4.0 * nnz + vb * nnz          // CSR (values only for general weights)
+                   + vb * (qmax + 1) * ldb                       // Lanczos basis
+                   + vb * 4.0 * n                                // Y, v, cdiag, dvec
+                   + 2.0 * vb * n * p.R                          // Omega, S
+                   + 16.0 * n                                    // z, y
+                   + 2.0 * 16.0 * n * p.R                        // reconstruction Y, U (FP64)
+                   + 56.0 * p.T_max + 8.0 * 65 * 1216 + 65536;   // history, partials, scalars
+    return (size_t)(bytes * 1.15);
+}
+
+}  // namespace
+
+struct scgal_server {
+    size_t budget = 0;
+    int max_slots = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request> queue;
+    std::map<uint64_t, scgal_result> done;
+    std::vector<Slot> slots;
+    std::thread worker;
+    bool stopping = false;
+    uint64_t next_id = 1;
+    size_t in_use = 0, peak = 0;
+    long long submitted = 0, admitted = 0, completed = 0, rejected = 0;
+    int active = 0;
+    static constexpr int CHUNK = 8;          // iterations per slot per round
+    static constexpr size_t QUEUE_MAX = 1 << 16;
+
+    void publish(Slot& s, int status, const scgal_stats* st) {
+        scgal_result r;
+        std::memset(&r, 0, sizeof(r));
+        r.status = status;
+        r.n = s.req.n;
+        if (st) {
+            r.iterations = st->converged ? st->t - 1 : st->t;
+            r.relgap = st->relgap;
+            r.infeas = st->infeas;
+            r.objective = st->p;
+        }
+        if (status >= 0 && s.h) {
+            std::vector<double> lam(s.req.prm.R), err(s.req.prm.R);
+            int64_t cut = 0;
+            const int rc = scgal_reconstruct(s.h, nullptr, lam.data(), err.data(), &cut);
+            if (rc == SCGAL_OK) {
+                r.best_cut = cut;
+                r.lambda_max = lam[0];
+            } else {
+                r.status = rc;
+            }
+        }
+        const double t = now_ms();
+        r.queue_ms = s.req.t_admit - s.req.t_submit;
+        r.latency_ms = t - s.req.t_submit;
+        if (s.h) scgal_destroy(s.h);
+        s.h = nullptr;
+        std::lock_guard<std::mutex> lk(mu);
+        done[s.req.id] = r;
+        in_use -= s.req.footprint;
+        s.active = false;
+        --active;
+        ++completed;
+        cv_done.notify_all();
+    }
+
+    void run() {
+        for (;;) {
+            // 1. admission
+            std::vector<int> fresh;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                while (stopping && !queue.empty()) {   // stop admitting: queued requests end unsolved
+                    scgal_result res;
+                    std::memset(&res, 0, sizeof(res));
+                    res.status = SCGAL_ESTATE;
+                    res.n = queue.front().n;
+                    done[queue.front().id] = res;
+                    ++rejected;
+                    queue.pop_front();
+                    cv_done.notify_all();
+                }
+                if (active == 0 && queue.empty()) {
+                    if (stopping) return;
+                    cv_work.wait_for(lk, std::chrono::milliseconds(50));
+                    continue;
+                }
+                for (int i = 0; i < max_slots && !queue.empty(); ++i) {
+                    if (slots[i].active) continue;
+                    Request& r = queue.front();
+                    if (in_use + r.footprint > budget) {
+                        if (active == 0 && r.footprint > budget) {   // can never fit: reject
+                            scgal_result res;
+                            std::memset(&res, 0, sizeof(res));
+                            res.status = SCGAL_ENOMEM;
+                            res.n = r.n;
+                            done[r.id] = res;
+                            ++rejected;
+                            queue.pop_front();
+                            cv_done.notify_all();
+                            --i;
+                            continue;
+                        }
+                        break;
+                    }
+                    slots[i].req = std::move(r);
+                    queue.pop_front();
+                    slots[i].active = true;
+                    slots[i].h = nullptr;
+                    in_use += slots[i].req.footprint;
+                    peak = std::max(peak, in_use);
+                    ++active;
+                    ++admitted;
+                    fresh.push_back(i);
+                }
+            }
+            for (int i : fresh) {
+                Slot& s = slots[i];
+                s.req.t_admit = now_ms();
+                const int rc = scgal_create_maxcut(s.req.row_ptr.data(), s.req.col.data(),
+                                                   s.req.has_w ? s.req.w.data() : nullptr, s.req.n, s.req.nnz, 0.0,
+                                                   &s.req.prm, &s.h);
+                if (rc) {
+                    s.h = nullptr;
+                    publish(s, rc, nullptr);
+                }
+            }
+            // 2. one chunk of every resident solve, all enqueued before any wait
+            std::vector<int> live;
+            for (int i = 0; i < max_slots; ++i) {
+                Slot& s = slots[i];
+                if (!s.active || !s.h) continue;
+                const int rc = scgal::launch_iterations(s.h, s.h->t_next + CHUNK - 1);
+                if (rc) publish(s, rc, nullptr);
+                else live.push_back(i);
+            }
+            // 3. wait, retire
+            for (int i : live) {
+                Slot& s = slots[i];
+                scgal_stats st;
+                std::memset(&st, 0, sizeof(st));
+                int conv = 0;
+                const int rc = scgal::finish_iterations(s.h, &st, &conv);
+                if (rc) publish(s, rc, nullptr);
+                else if (conv) publish(s, SCGAL_OK, &st);
+                else if (s.h->t_next > s.req.prm.T_max) publish(s, SCGAL_ENOTDONE, &st);
+            }
+        }
+    }
+};
+
+extern "C" {
+
+int scgal_server_create(size_t hbm_budget, int32_t max_slots, scgal_srv_t* out) {
+    if (!out || max_slots < 1 || max_slots > 256 || hbm_budget == 0) return SCGAL_EINVAL;
+    scgal_server* s = new scgal_server();
+    s->budget = hbm_budget;
+    s->max_slots = max_slots;
+    s->slots.resize(max_slots);
+    s->worker = std::thread([s] { s->run(); });
+    *out = s;
+    return SCGAL_OK;
+}
+
+int scgal_submit(scgal_srv_t s, const int32_t* row_ptr, const int32_t* col, const double* w, int32_t n, int64_t nnz,
+                 const scgal_params* params, uint64_t* ticket) {
+    if (!s || !row_ptr || (nnz > 0 && !col) || !params || !ticket || n < 2 || nnz < 0) return SCGAL_EINVAL;
+    if (params->T_max < 1 || params->R < 1 || params->R > SCGAL_RMAX) return SCGAL_EINVAL;
+    Request r;
+    r.n = n;
+    r.nnz = nnz;
+    r.prm = *params;
+    r.row_ptr.resize((size_t)n + 1);
+    r.col.resize((size_t)nnz);
+    // the caller's buffers may be host or device memory
+    if (cudaMemcpy(r.row_ptr.data(), row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDefault) != cudaSuccess ||
+        (nnz && cudaMemcpy(r.col.data(), col, sizeof(int32_t) * nnz, cudaMemcpyDefault) != cudaSuccess)) {
+        cudaGetLastError();
+        return SCGAL_ECUDA;
+    }
+    if (w) {
+        r.has_w = true;
+        r.w.resize((size_t)nnz);
+        if (nnz && cudaMemcpy(r.w.data(), w, sizeof(double) * nnz, cudaMemcpyDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return SCGAL_ECUDA;
+        }
+    }
+    r.footprint = estimate_footprint(n, nnz, *params);
+    r.t_submit = now_ms();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stopping) return SCGAL_ESTATE;
+    if (s->queue.size() >= scgal_server::QUEUE_MAX) return SCGAL_EBUSY;
+    r.id = s->next_id++;
+    *ticket = r.id;
+    ++s->submitted;
+    s->queue.push_back(std::move(r));
+    s->cv_work.notify_one();
+    return SCGAL_OK;
+}
+
+int scgal_poll(scgal_srv_t s, uint64_t ticket, scgal_result* out, int32_t timeout_ms) {
+    if (!s || !out) return SCGAL_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto ready = [&] { return s->done.count(ticket) > 0; };
+    if (timeout_ms < 0) s->cv_done.wait(lk, ready);
+    else if (timeout_ms > 0) s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+    auto it = s->done.find(ticket);
+    if (it == s->done.end()) return SCGAL_ETIMEOUT;
+    *out = it->second;
+    s->done.erase(it);
+    return SCGAL_OK;
+}
+
+int scgal_server_get_stats(scgal_srv_t s, scgal_server_stats* out) {
+    if (!s || !out) return SCGAL_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->submitted = s->submitted;
+    out->admitted = s->admitted;
+    out->completed = s->completed;
+    out->rejected = s->rejected;
+    out->active = s->active;
+    out->queued = (int32_t)s->queue.size();
+    out->device_bytes_in_use = (int64_t)s->in_use;
+    out->device_bytes_peak = (int64_t)s->peak;
+    return SCGAL_OK;
+}
+
+int scgal_server_destroy(scgal_srv_t s) {
+    if (!s) return SCGAL_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+        s->cv_work.notify_all();
+    }
+    if (s->worker.joinable()) s->worker.join();
+    for (auto& sl : s->slots)
+        if (sl.h) scgal_destroy(sl.h);
+    delete s;
+    return SCGAL_OK;
+}
+
+}  // extern "C"

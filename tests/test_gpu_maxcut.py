@@ -1,0 +1,248 @@
+"""GPU parity of the MaxCut path against the FP64 oracle, through the C ABI.
+
+Tolerances (relative): single D-matvec 1e-5 (FP32 path) / 1e-12 (FP64 path);
+Lanczos Ritz value 1e-4 / 1e-10; end-of-run objective and infeasibility after T
+iterations 1e-3 (FP32; the trajectories are not bitwise equal) / 1e-7 (FP64);
+cut values exact integers for the same sign vector.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.lanczos import approx_min_evec, lanczos_steps
+from oracle.nystrom import NystromSketch
+from oracle.philox import PURPOSE_LANCZOS, PURPOSE_OMEGA, gaussian_matrix, gaussian_vector
+from oracle.problems import MaxCutProblem
+from oracle.rounding import cut_weight, round_maxcut
+from oracle.sketchycgal import sketchy_cgal
+
+pytestmark = pytest.mark.gpu
+
+TOL_MV = {32: 1e-5, 64: 1e-12}
+TOL_XI = {32: 1e-4, 64: 1e-10}
+TOL_E2E = {32: 1e-3, 64: 1e-7}
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_1912_02949_gb300 import build, scgal
+    build.build()
+    scgal.load()
+    return scgal
+
+
+def _handle(S, g, prec, R=10, T_max=100, seed=0, **kw):
+    rp, col, val = g.csr()
+    w = None if g.weight_kind == "unit" else val
+    p = S.scgal_params_default(R=R, T_max=T_max, precision=prec, seed=seed, **kw)
+    return S.scgal_create_maxcut(rp, col, w, g.n, col.size, 0.0, p)
+
+
+def _relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+GRAPHS = {
+    "er_unit": lambda: W.er_graph(3000, 12000, seed=1, weights="unit"),
+    "er_pm1": lambda: W.er_graph(5000, 15000, seed=2, weights="pm1"),
+    "er_real": lambda: W.er_graph(2000, 9000, seed=3, weights="real"),
+    "dense_rows": lambda: W.er_graph(300, 20000, seed=4, weights="pm1"),     # degree ~130: 32-lane rows
+    "torus": lambda: W.torus_longrange_graph(32, 64, 0.1, seed=5, weights="pm1"),
+}
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("gname", sorted(GRAPHS))
+def test_apply_D_matches_oracle(S, gname, prec):
+    g = GRAPHS[gname]()
+    h = _handle(S, g, prec)
+    prob = MaxCutProblem(g.n, g.i, g.j, g.w)
+    r = np.random.default_rng(7)
+    x = r.standard_normal(g.n)
+    w = 0.01 * r.standard_normal(g.n)
+    yg = S.scgal_apply_D(h, x, w)
+    yo = prob.C_apply(x) + prob.Astar_apply(w, x)
+    assert _relerr(yg, yo) <= TOL_MV[prec]
+    assert np.max(np.abs(yg - yo)) <= TOL_MV[prec] * np.max(np.abs(yo))
+    info = S.scgal_get_info(h)
+    assert info["weight_kind"] == {"unit": 0, "pm1": 1, "real": 2}[g.weight_kind]
+    assert math.isclose(info["normC"], prob.normC, rel_tol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_apply_D_edge_cases(S, prec):
+    # isolated vertices and a ragged tail of empty rows
+    g = W.er_graph(1000, 300, seed=9, weights="pm1")
+    h = _handle(S, g, prec)
+    prob = MaxCutProblem(g.n, g.i, g.j, g.w)
+    x = np.random.default_rng(1).standard_normal(g.n)
+    w = np.linspace(-1, 1, g.n)
+    assert _relerr(S.scgal_apply_D(h, x, w), prob.C_apply(x) + prob.Astar_apply(w, x)) <= TOL_MV[prec]
+    # empty graph (C = 0): D = diag(w);  smallest instance n = 2
+    for n, m in ((50, 0), (2, 1)):
+        g2 = W.er_graph(n, m, seed=0, weights="unit")
+        h2 = _handle(S, g2, prec)
+        p2 = MaxCutProblem(g2.n, g2.i, g2.j, g2.w)
+        x2 = np.arange(1.0, n + 1)
+        w2 = np.cos(np.arange(n))
+        assert _relerr(S.scgal_apply_D(h2, x2, w2), p2.C_apply(x2) + p2.Astar_apply(w2, x2)) <= TOL_MV[prec]
+
+
+def test_malformed_csr_is_rejected(S):
+    p = S.scgal_params_default(T_max=10)
+    rp = np.array([0, 2, 1, 3], dtype=np.int32)          # decreasing row pointer
+    col = np.array([1, 2, 0], dtype=np.int32)
+    with pytest.raises(S.ScgalError) as e:
+        S.scgal_create_maxcut(rp, col, None, 3, 3, 0.0, p)
+    assert e.value.status == S.SCGAL_EINVAL
+    rp = np.array([0, 1, 2, 3], dtype=np.int32)
+    for badcol in ([1, 7, 0], [0, 2, 1]):                 # out of range / diagonal entry
+        with pytest.raises(S.ScgalError):
+            S.scgal_create_maxcut(rp, np.array(badcol, dtype=np.int32), None, 3, 3, 0.0, p)
+    with pytest.raises(S.ScgalError):
+        S.scgal_create_maxcut(rp, np.array([1, 2, 0], dtype=np.int32), np.array([1.0, np.nan, 1.0]), 3, 3, 0.0, p)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("q", [1, 7, 40])
+def test_lanczos_matches_oracle(S, prec, q):
+    g = W.er_graph(4000, 14000, seed=11, weights="pm1")
+    h = _handle(S, g, prec, T_max=10 ** 6)
+    prob = MaxCutProblem(g.n, g.i, g.j, g.w)
+    r = np.random.default_rng(3)
+    w = 0.02 * r.standard_normal(g.n) - 0.01
+    t = 5
+    xi_g, k, v_g = S.scgal_lanczos(h, t, q, w)
+    v1 = gaussian_vector(0, PURPOSE_LANCZOS, t, 0, g.n, False)
+    xi_o, v_o, info = approx_min_evec(lambda u: prob.C_apply(u) + prob.Astar_apply(w, u), v1, q)
+    assert k == info["k"] == q
+    assert abs(xi_g - xi_o) <= TOL_XI[prec] * abs(xi_o)
+    v_o = v_o / np.linalg.norm(v_o)
+    assert abs(np.linalg.norm(v_g) - 1.0) < 1e-6
+    # the Ritz vectors agree up to sign
+    assert abs(abs(np.dot(v_g, v_o)) - 1.0) <= (1e-3 if prec == 32 else 1e-9)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_end_to_end_er800(S, prec):
+    """The n = 800, 19,176-edge Erdos-Renyi MaxCut SDP (smallest Gset shape), T = 500."""
+    g = W.config_graph("er800")
+    T = 500
+    h = _handle(S, g, prec, R=10, T_max=T)
+    prob = MaxCutProblem(g.n, g.i, g.j, g.w)
+    ref = sketchy_cgal(prob, R=10, T=T, seed=0)
+    rc, last = S.scgal_solve(h, T)
+    assert rc == S.SCGAL_ENOTDONE and last["t"] == T
+    hist = S.scgal_history(h, 1, T)
+    assert [r["q"] for r in hist] == [r["q"] for r in ref.history]
+    ro = ref.history[-1]
+    assert abs(last["p"] - ro["p_orig"]) <= TOL_E2E[prec] * abs(ro["p_orig"])
+    assert abs(last["infeas"] - ro["infeas"]) <= TOL_E2E[prec] * ro["infeas"]
+    assert abs(last["relgap"] - ro["relgap"]) <= 10 * TOL_E2E[prec] * max(abs(ro["relgap"]), 1e-3)
+    # early iterations follow the same path closely
+    for rg, rr in zip(hist[:5], ref.history[:5]):
+        assert abs(rg["xi"] - rr["xi"]) <= TOL_XI[prec] * abs(rr["xi"])
+    U, lam, err, cut = S.scgal_reconstruct(h)
+    np.testing.assert_allclose(lam[:3], ref.Lam[:3], rtol=(1e-2 if prec == 32 else 1e-6))
+    assert math.isclose(lam.sum(), ref.Lam.sum(), rel_tol=1e-9)       # trace correction: tr = alpha
+    # the GPU's cut is exactly the oracle's evaluation of the GPU's sign vectors
+    best, col, cuts = round_maxcut(U.T, g.i, g.j, g.w)
+    assert cut == best
+    # and close to the oracle's own rounding
+    best_o, _, _ = round_maxcut(ref.U, g.i, g.j, g.w)
+    assert abs(cut - best_o) <= 0.02 * best_o
+
+
+def test_cut_value_exact(S):
+    for weights in ("unit", "pm1"):
+        g = W.er_graph(20000, 70000, seed=21, weights=weights)
+        h = _handle(S, g, 32)
+        r = np.random.default_rng(5)
+        for _ in range(3):
+            chi = np.where(r.random(g.n) < 0.5, -1, 1).astype(np.int8)
+            assert S.scgal_cut_value(h, chi) == cut_weight(g.i, g.j, g.w, chi)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_nystrom_reconstruct_matches_oracle(S, prec):
+    """Alg. B.1 on a planted rank-3 psd X with the handle's own Omega."""
+    n, R = 3000, 8
+    g = W.er_graph(n, 9000, seed=2, weights="unit")
+    h = _handle(S, g, prec, R=R, scale=0)       # unscaled: alpha = n, no X scaling on output
+    Om = gaussian_matrix(0, PURPOSE_OMEGA, 0, n, R, False)
+    if prec == 32:
+        Om = Om.astype(np.float32).astype(np.float64)
+    r = np.random.default_rng(4)
+    Q, _ = np.linalg.qr(r.standard_normal((n, 3)))
+    ev = np.array([500.0, 200.0, 100.0])
+    Sk = (Q * ev) @ (Q.T @ Om)
+    tau = float(ev.sum())
+    S.scgal_set_state(h, S=Sk, tau=tau, t=1)
+    sk = NystromSketch(Om)
+    sk.S = Sk.astype(np.float32).astype(np.float64) if prec == 32 else Sk
+    sk.tau = tau
+    Uo, Lo, eo = sk.reconstruct()
+    U, lam, err, _ = S.scgal_reconstruct(h, want_cut=False)
+    # the trace correction (default on for MaxCut) shifts all R values by (alpha - tr)/R
+    shift = (n - Lo.sum()) / R
+    tol = 1e-4 if prec == 32 else 1e-8
+    np.testing.assert_allclose(lam[:3] - shift, Lo[:3], rtol=tol)
+    np.testing.assert_allclose(err[:3], eo[:3], rtol=tol, atol=tol * tau)
+    for c in range(3):
+        assert abs(abs(np.dot(U[c], Uo[:, c])) - 1.0) <= tol
+
+
+def test_checkpoint_resume_is_bitwise(S):
+    g = W.er_graph(3000, 10000, seed=8, weights="pm1")
+    a = _handle(S, g, 32, T_max=60)
+    S.scgal_solve(a, 30)
+    st = S.scgal_get_state(a)
+    S.scgal_solve(a, 50)
+    ra = S.scgal_history(a, 31, 20)
+    b = _handle(S, g, 32, T_max=60)
+    S.scgal_set_state(b, z=st["z"], y=st["y"], S=st["S"], p=st["p"], tau=st["tau"], t=st["t"])
+    S.scgal_solve(b, 50)
+    rb = S.scgal_history(b, 31, 20)
+    assert ra == rb
+
+
+def test_stopping_rule_and_state_errors(S):
+    g = W.cycle_graph(8)
+    h = _handle(S, g, 64, R=4, T_max=5000, tol=1e-3)
+    prob = MaxCutProblem(g.n, g.i, g.j, g.w)
+    ref = sketchy_cgal(prob, R=4, T=5000, seed=0, tol=1e-3)
+    rc, last = S.scgal_solve(h, 5000)
+    assert rc == S.SCGAL_OK and last["converged"] == 1
+    assert abs(last["t"] - ref.converged_at) <= 2
+    assert last["relgap"] <= 1e-3 and last["infeas"] <= 1e-3
+    with pytest.raises(S.ScgalError) as e:
+        S.scgal_step(h)
+    assert e.value.status == S.SCGAL_ESTATE
+
+
+def test_full_size_er2p20_matvec_and_first_iterations(S):
+    """n = 2^20, m = 3n, +/-1 weights (the bench workload) in the bench's launch
+    shape: sampled rows of one D-matvec, then three FP64 iterations vs the oracle."""
+    g = W.config_graph("er2p20")
+    prob = MaxCutProblem(g.n, g.i, g.j, g.w)
+    r = np.random.default_rng(0)
+    x = r.standard_normal(g.n)
+    w = 1e-3 * r.standard_normal(g.n)
+    yo = prob.C_apply(x) + prob.Astar_apply(w, x)
+    for prec in (32, 64):
+        h = _handle(S, g, prec, R=10, T_max=2000)
+        yg = S.scgal_apply_D(h, x, w)
+        assert _relerr(yg, yo) <= TOL_MV[prec]
+        h.close()
+    T = 3
+    ref = sketchy_cgal(prob, R=10, T=T, seed=0)
+    h = _handle(S, g, 64, R=10, T_max=2000)
+    S.scgal_solve(h, T)
+    st = S.scgal_get_state(h)
+    np.testing.assert_allclose(st["z"], ref.z, rtol=1e-8, atol=1e-14)
+    np.testing.assert_allclose(st["y"], ref.y, rtol=1e-8, atol=1e-14)
+    hist = S.scgal_history(h, 1, T)
+    for rg, rr in zip(hist, ref.history):
+        assert abs(rg["xi"] - rr["xi"]) <= 1e-9 * abs(rr["xi"])
