@@ -54,11 +54,14 @@ class MaxCutProblem:
     def _set_scale(self, scale: bool):
         self.scaled = bool(scale)
         if scale:
-            self.sC = 1.0 / self.normC
+            # Eq. 7.1 divides C by ||C||_F; when C = 0 (a graph without edges)
+            # there is nothing to normalise and C' = C.
+            cnorm = self.normC if self.normC > 0.0 else 1.0
+            self.sC = 1.0 / cnorm
             self.sA = 1.0 / self.normA
             self.alpha = 1.0
             self.b = self.b_orig / (self.alpha_orig * self.normA)
-            self.obj_factor = self.alpha_orig * self.normC   # <C,X> = obj_factor * <C',X'>
+            self.obj_factor = self.alpha_orig * cnorm        # <C,X> = obj_factor * <C',X'>
             self.z_factor = self.alpha_orig * self.normA     # AX - b = z_factor * (A'X' - b')
             self.X_factor = self.alpha_orig                  # X = X_factor * X'
             self.normA_s = 1.0
