@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 SketchyCGAL library (libscgal) on its headline workload.
+
+Workload (the single-GPU MaxCut configuration): random sparse graph
+G(n = 2^20, m = 3n) with weights +1/-1 (50/50), CSR int32, sketch rank R = 10,
+T = 2000 iterations of Alg. 6.1, FP32 vectors / matvecs / sketch with FP64
+reductions and dual state; compared against the FP64 path of the same library.
+
+One step = one full solve through the C ABI: create the handle from the CSR
+(already resident in HBM), T iterations, Nystrom reconstruction and rounding.
+`value` is iterations per second over all ranks (replicas on N GPUs, weak
+scaling).  `e2e` repeats the solve from host buffers with the host<->device
+copies inside the timed region.  The reference arm (`--impl reference`) times
+the FP64 CPU oracle on a bounded sample of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SketchyCGAL iter/s FP32 vs FP64 at equal gap; batched solves/s, p50/p99 ms"
+WORKLOAD = "maxcut_er2p20"
+N, R, T_DEFAULT, SEED = 1 << 20, 10, 2000, 0
+WORKLOAD_DESC = ("MaxCut SDP, G(n=2^20, m=3*2^20) with +1/-1 weights (50/50), CSR int32, "
+                 "R=10, T=2000, beta0=1, eta=2/(t+1), q_t=ceil(t^(1/4) ln n), seed 0")
+L2_NOTE = ("a 256 MB device buffer is written between timed solves (L2 flush); one solve's working set "
+           "(Lanczos basis 94 x 4 MB, Omega and S 2 x 40 MB, CSR 29 MB) exceeds the 129 MB L2")
+
+
+def lanczos_q(t: int, n: int) -> int:
+    return int(min(math.ceil(t ** 0.25 * math.log(n)), n - 1))
+
+
+def launches_per_solve(n: int, T: int) -> int:
+    """Kernels of one solve: per iteration 2q+3 (q D-matvec steps, q-1 updates,
+    tridiagonal, Ritz, fused z/sketch update, dual+start); create 6; reconstruct 13."""
+    return sum(2 * lanczos_q(t, n) + 3 for t in range(1, T + 1)) + 6 + 13
+
+
+def spmv_bytes(n: int, nnz: int) -> int:
+    """Algorithmic bytes of one D-matvec step (FP32, signs packed in the column
+    index): row_ptr 4(n+1) + col 4 nnz + x 4n (each entry at least once) +
+    dvec 4n + output 4n."""
+    return 4 * (n + 1) + 4 * nnz + 12 * n
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("k_maxcut.cu", "common.cuh", "internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1912_02949_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the D-matvec step from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "spmv_step_er2p20.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    try:
+        return int(float(vals["dram_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_sample(iters: int, reps: int) -> dict:
+    """Time the FP64 oracle on the first `iters` iterations of the workload, `reps`
+    times, plus a T = 1 run whose time is the fixed cost of a solve (test matrix,
+    reconstruction) plus one iteration.  Runs in a child process with one thread
+    per BLAS / OpenMP pool."""
+    import workloads as W
+    from oracle.lanczos import lanczos_steps
+    from oracle.problems import MaxCutProblem
+    from oracle.sketchycgal import sketchy_cgal
+
+    g = W.config_graph("er2p20", seed=SEED)
+    prob = MaxCutProblem(g.n, g.i, g.j, g.w)
+    t0 = time.perf_counter()
+    sketchy_cgal(prob, R=R, T=1, seed=SEED)
+    one = time.perf_counter() - t0
+    samples = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        sketchy_cgal(prob, R=R, T=iters, seed=SEED)
+        samples.append(time.perf_counter() - t0)
+    return {"iters": iters, "fixed_plus_one": one, "samples": samples,
+            "q_first": lanczos_steps(g.n, 1), "q_sum": sum(lanczos_steps(g.n, t) for t in range(1, iters + 1))}
+
+
+def run_cpu_sample(iters: int, reps: int = 1) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(iters),
+                          "--cpu-reps", str(reps)], capture_output=True, text=True, env=env, check=True).stdout
+    return json.loads(out.strip().splitlines()[-1])
+
+
+def oracle_rate(sample: dict, T: int) -> float:
+    """Oracle iterations/s on the full T-iteration run: seconds per iteration of
+    iterations 2..iters (fixed cost removed), scaled by the ratio of Lanczos
+    steps per iteration (the dominant cost) between the full run and the sample."""
+    k = sample["iters"]
+    per_iter = (statistics.median(sample["samples"]) - sample["fixed_plus_one"]) / (k - 1)
+    q_sample = (sample["q_sum"] - sample["q_first"]) / (k - 1)
+    q_full = sum(lanczos_q(t, N) for t in range(1, T + 1)) / T
+    return 1.0 / (per_iter * q_full / q_sample)
+
+
+def cpu_baseline_entry(sample: dict, T: int) -> dict:
+    secs = sum(sample["samples"]) + sample["fixed_plus_one"]
+    return {"value": oracle_rate(sample, T), "unit": "iter/s", "cores": 1, "kind": "oracle",
+            "sample": (f"iterations 2..{sample['iters']} of the same n=2^20 solve on one host core "
+                       f"({len(sample['samples'])} run(s) of T={sample['iters']} minus a T=1 run, {secs:.1f} s "
+                       f"in total); rate scaled to the full T={T} run by Lanczos steps per iteration")}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host, a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample = run_cpu_sample(args.sample_iters, args.steps)
+    rate = oracle_rate(sample, args.T)
+    cb = cpu_baseline_entry(sample, args.T)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "iter/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * args.T / rate,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "T": args.T},
+            "cpu_baseline": cb,
+            "e2e": {"value": rate, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--T", type=int, default=T_DEFAULT)
+    ap.add_argument("--sample-iters", type=int, default=6)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-reps", type=int, default=1, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.cpu_sample:
+        print(json.dumps(cpu_sample(args.cpu_sample, args.cpu_reps)))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1912_02949_gb300 import build, scgal as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if not os.path.exists(S.LIB_PATH):
+        build.build()
+    S.load()
+    T = args.T
+
+    g = W.config_graph("er2p20", seed=SEED)
+    rp, col, val = g.csr()
+    n, nnz = g.n, int(col.size)
+    d_rp = torch.from_numpy(rp).to(dev)
+    d_col = torch.from_numpy(col).to(dev)
+    d_w = torch.from_numpy(val).to(dev)
+    U_dev = torch.empty((R, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def params(prec, tol=0.0):
+        return S.scgal_params_default(R=R, T_max=T, precision=prec, seed=SEED + rank, tol=tol, device=local)
+
+    def solve(prec, host=False, tol=0.0, keep=False):
+        """One full solve; returns (ms, last record, best cut, lambda, handle or None)."""
+        bufs = (rp_h, col_h, w_h, U_h) if host else (d_rp, d_col, d_w, U_dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = S.scgal_create_maxcut(bufs[0], bufs[1], bufs[2], n, nnz, 0.0, params(prec, tol))
+        S.scgal_set_stream(h, stream.cuda_stream)
+        rc, last = S.scgal_solve(h, T)
+        U, lam, err, cut = S.scgal_reconstruct(h, U=bufs[3])
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        hist = S.scgal_history(h, 1, min(T, last["t"])) if keep else None
+        h.close()
+        return ms, last, cut, lam, hist
+
+    rp_h = torch.from_numpy(rp).pin_memory()
+    col_h = torch.from_numpy(col).pin_memory()
+    w_h = torch.from_numpy(val).pin_memory()
+    U_h = torch.empty((R, n), dtype=torch.float64).pin_memory()
+
+    for _ in range(args.warmup):
+        solve(32)
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, last = [], None
+    hist32 = None
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        ms, last, cut, lam, hh = solve(32, keep=(k == args.steps - 1))
+        times.append(ms)
+        if hh is not None:
+            hist32 = hh
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.barrier()
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * args.steps * T / (total_ms / 1000.0)
+
+    extra = {}
+    # the plain FP64 GPU path on the same solve, and both paths to relative gap <= 1e-3
+    if not args.no_fp64:
+        solve(64)
+        ms64, last64, cut64, _, _ = solve(64)
+        extra["fp64"] = {"iter_per_s": T / (ms64 / 1000.0), "relgap_T": last64["relgap"],
+                         "infeas_T": last64["infeas"], "best_cut": cut64, "ms_per_solve": ms64}
+        gap = {}
+        for prec in (32, 64):
+            ms_g, last_g, _, _, _ = solve(prec, tol=1e-3)
+            it = last_g["t"] - 1 if last_g["converged"] else last_g["t"]
+            gap[f"fp{prec}"] = {"converged": bool(last_g["converged"]), "iterations": it,
+                                "seconds": ms_g / 1000.0, "relgap": last_g["relgap"], "infeas": last_g["infeas"]}
+        extra["equal_gap_1e-3"] = gap
+        extra["fp32_over_fp64"] = value / world / extra["fp64"]["iter_per_s"]
+
+    # end to end from host buffers (pinned), copies inside the timed region
+    ms_e2e, last_e, _, _, _ = solve(32, host=True)
+    e2e = {"value": T / (ms_e2e / 1000.0), "unit": "iter/s",
+           "h2d_bytes_per_step": 4 * (n + 1) + 4 * nnz + 8 * nnz,
+           "d2h_bytes_per_step": 8 * n * R + 16 * R + 8}
+
+    # dominant kernel: the D-matvec step, timed with CUDA events on its stream
+    h = S.scgal_create_maxcut(d_rp, d_col, d_w, n, nnz, 0.0, params(32))
+    S.scgal_solve(h, T // 2)
+    kern = {}
+    for kid, name in ((0, "spmv_step"), (1, "lanczos_update"), (2, "ritz"), (3, "tridiag")):
+        kern[name] = S.scgal_time_kernel(h, kid, 200 if kid < 2 else 20)
+    info = S.scgal_get_info(h)
+    h.close()
+    peak, peak_src = measured_peaks()
+    bytes_step = spmv_bytes(n, nnz)
+    achieved = bytes_step / (kern["spmv_step"] * 1e-3) / 1e9
+    qs = [lanczos_q(t, n) for t in range(1, T + 1)]
+    per_solve_ms = sum(times) / args.steps
+    share = {"spmv_step": kern["spmv_step"] * sum(qs) / per_solve_ms,
+             "lanczos_update": kern["lanczos_update"] * (sum(qs) - T) / per_solve_ms,
+             "ritz": kern["ritz"] * T / per_solve_ms, "tridiag": kern["tridiag"] * T / per_solve_ms}
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(), "kernel": "k_spmv_step (CSR D-matvec + omega reduction)",
+                "bytes_per_launch": bytes_step, "ms_per_launch": kern["spmv_step"], "peak_source": peak_src}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_entry(run_cpu_sample(args.sample_iters), T)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "n": n, "m": g.m, "nnz": nnz, "R": R,
+                           "T": T, "precision": "fp32 vectors/matvec/sketch, fp64 reductions and dual state",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "l2": L2_NOTE, "spmv_lanes_per_row": info["spmv_group"]},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * launches_per_solve(n, T),
+                "clocks": clk, "solve": {"relgap_T": last["relgap"], "infeas_T": last["infeas"],
+                                         "objective_T": last["p"], "best_cut": cut, "lambda_top3": list(lam[:3])},
+                "kernels_ms_per_launch": kern, "kernel_share_of_solve": share, **extra}
+        if hist32:
+            hit = next((r["t"] for r in hist32 if r["relgap"] <= 1e-3 and r["infeas"] <= 1e-3), None)
+            line["solve"]["first_t_gap_1e-3"] = hit
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -69,6 +69,9 @@ typedef struct {
     uint64_t seed;          /* seeds Omega and every Lanczos start vector */
     uint32_t instance;      /* stream id of this instance's random draws (default 0) */
     int32_t  check_every;   /* scgal_solve reads the stopping flag every k iterations (default 16) */
+    int32_t  device;        /* CUDA device ordinal of the handle; -1 = device 0 (default -1).
+                               The library sets it itself on every call, independently of
+                               the caller's current device. */
 } scgal_params;
 
 /* One iteration record (Alg. 6.1 step t; stopping values of Eq. E.1 for the
@@ -187,6 +190,16 @@ int scgal_set_state(scgal_t h, const double* z, const double* y, const double* S
 int scgal_history(scgal_t h, int64_t first, int64_t count, scgal_stats* out);
 
 int scgal_get_info(scgal_t h, scgal_info* out);
+
+/* Measurement: launch one of the iteration's kernels `reps` times back to back
+ * on the handle's stream between two CUDA events and report the mean duration
+ * of one launch in milliseconds.  kernel: 0 the Lanczos D-matvec step (MaxCut:
+ * CSR pass fused with the omega reduction; phase retrieval: the three FFT
+ * passes), 1 the three-term update, 2 the Ritz vector, 3 the tridiagonal
+ * eigensolver.  Works on the iteration t the handle is about to run, with
+ * private scalars: the solver state is unchanged (only per-iteration scratch
+ * is overwritten), so call it between iterations. */
+int scgal_time_kernel(scgal_t h, int32_t kernel, int32_t reps, double* ms_per_launch);
 
 /* Use `stream` (a cudaStream_t) for all of the handle's work instead of its own. */
 int scgal_set_stream(scgal_t h, void* stream);

@@ -172,9 +172,16 @@ scgal_ctx* new_ctx(const scgal_params* prm, int kind) {
     h->prm = *prm;
     h->kind = kind;
     h->prec = prm->precision;
-    cudaGetDevice(&h->device);
+    h->device = prm->device >= 0 ? prm->device : 0;
+    cudaSetDevice(h->device);
     return h;
 }
+
+// Every call on a handle first makes the handle's device current (for the
+// library's own runtime state, which is independent of the caller's).
+struct DeviceGuard {
+    explicit DeviceGuard(const scgal_ctx* h) { cudaSetDevice(h->device); }
+};
 
 int check_params(const scgal_params* p) {
     if (!p) return SCGAL_EINVAL;
@@ -183,6 +190,13 @@ int check_params(const scgal_params* p) {
     if (p->precision != 32 && p->precision != 64) return SCGAL_EINVAL;
     if (!(p->beta0 > 0.0)) return SCGAL_EINVAL;
     if (p->check_every < 1) return SCGAL_EINVAL;
+    if (p->device >= 0) {
+        int count = 0;
+        if (cudaGetDeviceCount(&count) != cudaSuccess || p->device >= count) {
+            cudaGetLastError();
+            return SCGAL_EINVAL;
+        }
+    }
     return SCGAL_OK;
 }
 
@@ -691,6 +705,55 @@ int do_lanczos(scgal_ctx* h, const double* w, long long t, int q, double* xi, in
 }
 
 template <typename V>
+int do_time_kernel(scgal_ctx* h, int kernel, int reps, double* ms) {
+    int rc = ensure_aux<V>(h);
+    if (rc) return rc;
+    AuxView a = aux_view<V>(h);
+    KP<V> p = kp<V>(h);   // private scalars and history slot: the solver state is not touched
+    cudaStream_t s = h->stream;
+    p.sc = a.sc;
+    p.hist = a.hist;
+    p.c.hist_cap = 1;
+    p.c.tol = 0.0;
+    const long long t = h->t_next;
+    const int q = std::min(lanczos_q(t, h->n), h->qmax);
+    auto step = [&](int i) {
+        if constexpr (VT<V>::cplx) launch_phase_step<V>(p, i, s);
+        else launch_spmv_step<V>(p, h->grid_spmv, h->spmv_group, i, s);
+    };
+    CUDA_TRY(h, cudaMemsetAsync(a.sc, 0, sizeof(DevScalars), s));
+    launch_start_only<V>(p, h->grid_elem, t, s);
+    if (kernel >= 2) {   // a full Lanczos run first, so T and the basis are q deep
+        for (int i = 0; i < q; ++i) {
+            step(i);
+            if (i < q - 1) launch_lanczos_update<V>(p, h->grid_elem, i, s);
+        }
+        launch_tridiag<V>(p, q, s);
+    } else if (kernel == 1) {
+        step(0);
+    }
+    cudaEvent_t e0, e1;
+    CUDA_TRY(h, cudaEventCreate(&e0));
+    CUDA_TRY(h, cudaEventCreate(&e1));
+    CUDA_TRY(h, cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) {
+        if (kernel == 0) step(0);
+        else if (kernel == 1) launch_lanczos_update<V>(p, h->grid_elem, 0, s);
+        else if (kernel == 2) launch_ritz<V>(p, h->grid_elem, s);
+        else launch_tridiag<V>(p, q, s);
+    }
+    CUDA_TRY(h, cudaEventRecord(e1, s));
+    CUDA_TRY(h, cudaEventSynchronize(e1));
+    float el = 0.f;
+    cudaEventElapsedTime(&el, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_TRY(h, cudaGetLastError());
+    *ms = (double)el / reps;
+    return SCGAL_OK;
+}
+
+template <typename V>
 int do_get_state(scgal_ctx* h, double* z, double* y, double* S, double* scalars) {
     typedef typename VT<V>::R R;
     KP<V>& p = kp<V>(h);
@@ -863,6 +926,7 @@ int do_launch(scgal_ctx* h, long long T_end) {
 // Enqueue iterations t_next .. T_end without waiting (serving loop).
 int scgal::launch_iterations(scgal_ctx* h, long long T_end) {
     if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
     if (h->converged_host) return SCGAL_OK;
     if (T_end > h->prm.T_max) T_end = h->prm.T_max;
     return DISPATCH(h, do_launch, h, T_end);
@@ -871,6 +935,7 @@ int scgal::launch_iterations(scgal_ctx* h, long long T_end) {
 // Wait for the handle's queued work; reports convergence and the last record.
 int scgal::finish_iterations(scgal_ctx* h, scgal_stats* out, int* converged) {
     if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
     bool conv = h->converged_host != 0;
     int rc = conv ? SCGAL_OK : DISPATCH(h, after_run, h, h->t_next - 1, out, &conv);
     *converged = conv ? 1 : 0;
@@ -910,6 +975,7 @@ void scgal_params_default(scgal_params* p) {
     p->seed = 0;
     p->instance = 0;
     p->check_every = 16;
+    p->device = -1;
 }
 
 const char* scgal_strerror(int status) {
@@ -979,6 +1045,7 @@ int scgal_create_phase(const double* masks, int32_t L, int32_t n, const double* 
 int scgal_step(scgal_t h, scgal_stats* out) {
     if (!h) return SCGAL_EINVAL;
     if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
     if (h->converged_host || h->t_next > h->prm.T_max) return SCGAL_ESTATE;
     return DISPATCH(h, do_step, h, out);
 }
@@ -986,6 +1053,7 @@ int scgal_step(scgal_t h, scgal_stats* out) {
 int scgal_solve(scgal_t h, int64_t T, scgal_stats* out) {
     if (!h) return SCGAL_EINVAL;
     if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
     if (T > h->prm.T_max || T < 1) return SCGAL_EINVAL;
     if (h->converged_host) return SCGAL_OK;
     if (h->t_next > T) return SCGAL_ENOTDONE;
@@ -995,36 +1063,49 @@ int scgal_solve(scgal_t h, int64_t T, scgal_stats* out) {
 int scgal_reconstruct(scgal_t h, double* U, double* lambda, double* err, int64_t* best_cut) {
     if (!h) return SCGAL_EINVAL;
     if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
     return DISPATCH(h, do_reconstruct, h, U, lambda, err, best_cut);
 }
 
 int scgal_cut_value(scgal_t h, const int8_t* chi, int64_t* cut) {
     if (!h || !chi || !cut || h->kind != KIND_MAXCUT) return SCGAL_EINVAL;
     if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
     return DISPATCH(h, do_cut_value, h, chi, cut);
 }
 
 int scgal_apply_D(scgal_t h, const double* w, const double* x, double* out) {
     if (!h || !x || !out) return SCGAL_EINVAL;
     if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
     return DISPATCH(h, do_apply_D, h, w, x, out);
 }
 
 int scgal_lanczos(scgal_t h, const double* w, int64_t t, int32_t q, double* xi, int32_t* k, double* v) {
     if (!h || !xi || !k || !v || t < 1 || q < 1 || q > h->qmax || q > h->n - 1) return SCGAL_EINVAL;
     if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
     return DISPATCH(h, do_lanczos, h, w, (long long)t, q, xi, k, v);
+}
+
+int scgal_time_kernel(scgal_t h, int32_t kernel, int32_t reps, double* ms_per_launch) {
+    if (!h || !ms_per_launch || kernel < 0 || kernel > 3 || reps < 1) return SCGAL_EINVAL;
+    if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
+    return DISPATCH(h, do_time_kernel, h, kernel, reps, ms_per_launch);
 }
 
 int scgal_get_state(scgal_t h, double* z, double* y, double* S, double* scalars) {
     if (!h) return SCGAL_EINVAL;
     if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
     return DISPATCH(h, do_get_state, h, z, y, S, scalars);
 }
 
 int scgal_set_state(scgal_t h, const double* z, const double* y, const double* S, const double* scalars) {
     if (!h) return SCGAL_EINVAL;
     if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
     return DISPATCH(h, do_set_state, h, z, y, S, scalars);
 }
 
@@ -1032,6 +1113,7 @@ int scgal_history(scgal_t h, int64_t first, int64_t count, scgal_stats* out) {
     if (!h || !out || first < 1 || count < 0) return SCGAL_EINVAL;
     if (count > h->c.hist_cap || first + count - 1 >= h->t_next + 1) return SCGAL_EINVAL;
     if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
     return DISPATCH(h, do_history, h, (long long)first, (long long)count, out);
 }
 
@@ -1060,6 +1142,7 @@ int scgal_get_info(scgal_t h, scgal_info* out) {
 
 int scgal_set_stream(scgal_t h, void* stream) {
     if (!h) return SCGAL_EINVAL;
+    DeviceGuard guard(h);
     cudaStreamSynchronize(h->stream);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     h->own_stream = false;
@@ -1069,6 +1152,7 @@ int scgal_set_stream(scgal_t h, void* stream) {
 
 int scgal_destroy(scgal_t h) {
     if (!h) return SCGAL_EINVAL;
+    DeviceGuard guard(h);
     free_ctx(h);
     return SCGAL_OK;
 }

@@ -36,7 +36,7 @@ class ScgalError(RuntimeError):
 class scgal_params(Structure):
     _fields_ = [("R", c_int32), ("T_max", c_int32), ("tol", c_double), ("beta0", c_double), ("K", c_double),
                 ("lmo", c_int32), ("scale", c_int32), ("trace_correct", c_int32), ("precision", c_int32),
-                ("seed", c_uint64), ("instance", c_uint32), ("check_every", c_int32)]
+                ("seed", c_uint64), ("instance", c_uint32), ("check_every", c_int32), ("device", c_int32)]
 
 
 class scgal_stats(Structure):
@@ -88,6 +88,7 @@ _PROTOS = {
     "scgal_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "scgal_history": (c_int, [c_void_p, c_int64, c_int64, POINTER(scgal_stats)]),
     "scgal_get_info": (c_int, [c_void_p, POINTER(scgal_info)]),
+    "scgal_time_kernel": (c_int, [c_void_p, c_int32, c_int32, POINTER(c_double)]),
     "scgal_set_stream": (c_int, [c_void_p, c_void_p]),
     "scgal_destroy": (c_int, [c_void_p]),
     "scgal_strerror": (c_char_p, [c_int]),
@@ -288,6 +289,14 @@ def scgal_get_info(h: Handle) -> dict:
     inf = scgal_info()
     _check(load().scgal_get_info(h.raw, ctypes.byref(inf)), "scgal_get_info")
     return {f: getattr(inf, f) for f, _ in inf._fields_ if f != "reserved"}
+
+
+def scgal_time_kernel(h: Handle, kernel: int, reps: int) -> float:
+    """Mean milliseconds per launch of iteration kernel `kernel` (0 D-matvec step,
+    1 Lanczos update, 2 Ritz vector, 3 tridiagonal solve)."""
+    ms = c_double(0)
+    _check(load().scgal_time_kernel(h.raw, int(kernel), int(reps), ctypes.byref(ms)), "scgal_time_kernel")
+    return ms.value
 
 
 def scgal_set_stream(h: Handle, stream_ptr: int):
