@@ -81,9 +81,8 @@ int grid_for(long long work, int per_block, int cap_per_sm) {
 
 // ---------------------------------------------------------------------------
 template <typename V>
-void enqueue_iteration(scgal_ctx* h, int q) {
+void enqueue_iteration(scgal_ctx* h, int q, cudaStream_t s) {
     KP<V>& p = kp<V>(h);
-    cudaStream_t s = h->stream;
     for (int i = 0; i < q; ++i) {
         if constexpr (VT<V>::cplx) launch_phase_step<V>(p, i, s);
         else launch_spmv_step<V>(p, h->grid_spmv, h->spmv_group, i, s);
@@ -102,9 +101,11 @@ int run_iteration(scgal_ctx* h, int q) {
     cudaGraphExec_t ex;
     if (it == h->graphs.end()) {
         cudaGraph_t g;
-        CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        enqueue_iteration<V>(h, q);
-        CUDA_TRY(h, cudaStreamEndCapture(h->stream, &g));
+        // captured on a private stream: the caller's stream may be the legacy
+        // default stream, which cannot be captured; the graph runs on any stream
+        CUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_iteration<V>(h, q, h->cap_stream);
+        CUDA_TRY(h, cudaStreamEndCapture(h->cap_stream, &g));
         cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
         cudaGraphDestroy(g);
         CUDA_TRY(h, e);
@@ -891,6 +892,7 @@ void free_ctx(scgal_ctx* h) {
     if (h->flag_host) cudaFreeHost(h->flag_host);
     if (h->flag_event) cudaEventDestroy(h->flag_event);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->kp) {
         if (h->cplx) {
             if (h->prec == 32) delete_kp<float2>(h);
@@ -906,6 +908,7 @@ void free_ctx(scgal_ctx* h) {
 int common_open(scgal_ctx* h) {
     CUDA_TRY(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     h->own_stream = true;
+    CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CUDA_TRY(h, cudaHostAlloc((void**)&h->flag_host, sizeof(int) * 4, cudaHostAllocDefault));
     CUDA_TRY(h, cudaEventCreateWithFlags(&h->flag_event, cudaEventDisableTiming));
     return SCGAL_OK;

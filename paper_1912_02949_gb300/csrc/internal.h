@@ -120,6 +120,7 @@ struct scgal_ctx {
     int spmv_group = 8;
     int grid_elem = 1, grid_spmv = 1;
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream the iteration graphs are captured on
     bool own_stream = false;
     int sticky = 0;
     long long t_next = 1;       // host view of the next iteration index
