@@ -201,6 +201,39 @@ int scgal_get_info(scgal_t h, scgal_info* out);
  * is overwritten), so call it between iterations. */
 int scgal_time_kernel(scgal_t h, int32_t kernel, int32_t reps, double* ms_per_launch);
 
+/* Allocation-free D-matvec with its inner product.  The paper has no
+ * counterpart: this is a service of the library for callers that cannot
+ * allocate device memory -- a process whose device memory all belongs to one
+ * pool it manages itself (a serving runtime with a fixed budget), a framework
+ * whose allocations must all go through its own allocator, or a latency-bound
+ * loop that cannot afford the implicit synchronisation of cudaMalloc/cudaFree.
+ * Every other entry point allocates (the handle owns its state); this one does
+ * not, and calls no allocating CUDA or library routine.
+ *
+ * Computes, for a symmetric CSR graph with weights val (NULL = all 1),
+ *     y[r] = diag[r] * x[r] + coff * sum_{j in row r} val[j] * x[col[j]]
+ *     *dot = sum_r x[r] * y[r]      (FP64 sum in a fixed order: deterministic)
+ * which is the D-matvec step of the solver's Lanczos loop (MaxCut: diag = the
+ * diagonal of C' + A'*(w), coff = 1/(4 ||C||_F)).  All arrays are device memory
+ * owned by the caller: row_ptr[n+1], col[nnz] (0 <= col < n, not checked),
+ * val[nnz], diag[n], x[n], y[n] (written), dot (one double, written).  The work
+ * runs on `stream` (a cudaStream_t; NULL = the legacy default stream) on the
+ * GPU that holds x, and the call returns without waiting for it.
+ *
+ * Scratch: the reduction's per-block partial sums and arrival counter live in
+ * one static device array of 1 MB (plus 256 bytes) that every GPU which loads
+ * the library keeps until the process exits.  It bounds the size:
+ * n <= 1,048,576 rows (any degree); larger n, n < 1, a negative nnz, a NULL
+ * array or x not in device memory return SCGAL_EINVAL before anything runs.
+ * The first call on each device looks up the array's device address (a one-time
+ * set-up); make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (on different streams, or from several
+ * threads) race on it and give wrong results; serialise them.  The counter is
+ * cleared on the stream at the start of every call. */
+int scgal_dmatvec_noalloc(const int32_t* row_ptr, const int32_t* col, const float* val, const float* diag,
+                          float coff, int32_t n, int64_t nnz, const float* x, float* y, double* dot,
+                          void* stream);
+
 /* Use `stream` (a cudaStream_t) for all of the handle's work instead of its own. */
 int scgal_set_stream(scgal_t h, void* stream);
 

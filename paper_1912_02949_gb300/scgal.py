@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, Structure, c_char_p, c_double, c_int, c_int8, c_int32, c_int64, c_uint32, c_uint64, c_void_p, c_size_t
+from ctypes import POINTER, Structure, c_char_p, c_double, c_float, c_int, c_int8, c_int32, c_int64, c_uint32, c_uint64, c_void_p, c_size_t
 
 import numpy as np
 
@@ -90,6 +90,8 @@ _PROTOS = {
     "scgal_get_info": (c_int, [c_void_p, POINTER(scgal_info)]),
     "scgal_time_kernel": (c_int, [c_void_p, c_int32, c_int32, POINTER(c_double)]),
     "scgal_set_stream": (c_int, [c_void_p, c_void_p]),
+    "scgal_dmatvec_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_int32, c_int64, c_void_p,
+                                      c_void_p, c_void_p, c_void_p]),
     "scgal_destroy": (c_int, [c_void_p]),
     "scgal_strerror": (c_char_p, [c_int]),
     "scgal_server_create": (c_int, [c_size_t, c_int32, POINTER(c_void_p)]),
@@ -305,6 +307,14 @@ def scgal_set_stream(h: Handle, stream_ptr: int):
 
 def scgal_destroy(h: Handle):
     h.close()
+
+
+def scgal_dmatvec_noalloc(row_ptr, col, val, diag, coff: float, n: int, nnz: int, x, y, dot, stream: int = 0):
+    """y = diag .* x + coff * (W x) and dot = <x, y> without any device allocation
+    (all arguments are caller-owned CUDA tensors; see include/scgal.h)."""
+    _check(load().scgal_dmatvec_noalloc(_ptr(row_ptr), _ptr(col), _ptr(val), _ptr(diag), float(coff), int(n),
+                                        int(nnz), _ptr(x), _ptr(y), _ptr(dot), c_void_p(stream)),
+           "scgal_dmatvec_noalloc")
 
 
 # --- serving -----------------------------------------------------------------
