@@ -211,6 +211,28 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_solve(T: int):
+    """One FP32 solve of the workload through the C ABI (no timing, no extras)."""
+    import torch
+
+    import workloads as W
+    from paper_1912_02949_gb300 import scgal as S
+
+    S.load()
+    g = W.config_graph("er2p20", seed=SEED)
+    rp, col, val = g.csr()
+    dev = torch.device("cuda", 0)
+    d_rp, d_col, d_w = (torch.from_numpy(a).to(dev) for a in (rp, col, val))
+    h = S.scgal_create_maxcut(d_rp, d_col, d_w, g.n, int(col.size), 0.0,
+                              S.scgal_params_default(R=R, T_max=T, precision=32, seed=SEED))
+    t0 = time.perf_counter()
+    rc, last = S.scgal_solve(h, T)
+    S.scgal_reconstruct(h)
+    print(json.dumps({"T": T, "seconds": time.perf_counter() - t0, "relgap": last["relgap"],
+                      "launches": launches_per_solve(g.n, T)}))
+    h.close()
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -224,12 +246,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-reps", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="one untimed FP32 solve of T iterations of the workload (for ncu captures)")
     args = ap.parse_args()
     if args.cpu_sample:
         print(json.dumps(cpu_sample(args.cpu_sample, args.cpu_reps)))
         return
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_solve:
+        profile_solve(args.T)
         return
 
     import numpy as np
