@@ -89,7 +89,7 @@ void enqueue_iteration(scgal_ctx* h, int q, cudaStream_t s) {
         if (i < q - 1) launch_lanczos_update<V>(p, h->grid_elem, i, s);
     }
     launch_tridiag<V>(p, q, s);
-    launch_ritz<V>(p, h->grid_elem, s);
+    launch_ritz<V>(p, h->grid_ritz, s);
     if constexpr (VT<V>::cplx) launch_phase_update<V>(p, h->grid_elem, s);
     else launch_vcv_update<V>(p, h->grid_spmv, h->spmv_group, s);
     launch_dual_start<V>(p, h->grid_elem, 1, s);
@@ -160,6 +160,10 @@ int setup_state(scgal_ctx* h) {
     CUDA_TRY(h, cudaMemsetAsync(p.ticket, 0, sizeof(unsigned) * 4, s));
     CUDA_TRY(h, cudaMemsetAsync(p.hist, 0, sizeof(scgal_stats) * (size_t)hist_cap, s));
     CUDA_TRY(h, cudaMemsetAsync(p.basis, 0, sizeof(V) * (size_t)(h->qmax + 1) * h->ldb, s));
+    // launch shapes, queried here so that no API call happens inside a capture
+    prepare_lanczos_shapes<V>();
+    if constexpr (!VT<V>::cplx) prepare_maxcut_shapes<V>();
+    h->grid_ritz = std::min(h->grid_elem, ritz_resident<V>(p));
     launch_gen_omega<V>(p, grid_for((long long)n * R, SCGAL_BS, 8), s);
     launch_dual_start<V>(p, h->grid_elem, 0, s);
     CUDA_TRY(h, cudaGetLastError());
@@ -344,12 +348,11 @@ int maxcut_build(scgal_ctx* h, const int32_t* row_ptr, const int32_t* col, const
     p.cdiag = d_cdiag;
     p.dvec = d_dvec;
     // launch shape: G lanes per row, G = smallest power of two >= average degree
-    const double avg = n ? (double)nnz / n : 0.0;
-    int G = 2;
-    while (G < 32 && G < avg) G *= 2;
-    h->spmv_group = G;
-    h->grid_spmv = grid_for(n, SCGAL_BS / G, 8);
-    h->grid_elem = grid_for(n, SCGAL_BS, 4);
+    // launch shapes: the D-matvec takes a warp per 32 rows (8 chunks of rows in
+    // flight per block), the streaming kernels 16-byte groups per thread
+    h->spmv_group = 32;
+    h->grid_spmv = grid_for(n, SCGAL_BS, 6);
+    h->grid_elem = grid_for((n + 3) / 4, SCGAL_BS, 8);
     return setup_state<V>(h);
 }
 
@@ -690,7 +693,7 @@ int do_lanczos(scgal_ctx* h, const double* w, long long t, int q, double* xi, in
         if (i < q - 1) launch_lanczos_update<V>(p, h->grid_elem, i, s);
     }
     launch_tridiag<V>(p, q, s);
-    launch_ritz<V>(p, h->grid_elem, s);
+    launch_ritz<V>(p, h->grid_ritz, s);
     DevScalars hs;
     CUDA_TRY(h, cudaMemcpyAsync(&hs, a.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
@@ -740,7 +743,7 @@ int do_time_kernel(scgal_ctx* h, int kernel, int reps, double* ms) {
     for (int r = 0; r < reps; ++r) {
         if (kernel == 0) step(0);
         else if (kernel == 1) launch_lanczos_update<V>(p, h->grid_elem, 0, s);
-        else if (kernel == 2) launch_ritz<V>(p, h->grid_elem, s);
+        else if (kernel == 2) launch_ritz<V>(p, h->grid_ritz, s);
         else launch_tridiag<V>(p, q, s);
     }
     CUDA_TRY(h, cudaEventRecord(e1, s));

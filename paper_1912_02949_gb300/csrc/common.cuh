@@ -17,6 +17,17 @@
 #include <stdint.h>
 
 #define SCGAL_BS 256          // threads per block of every reduction kernel
+
+// Blocks of `kernel` (SCGAL_BS threads, `smem` dynamic bytes) that fit on the GPU
+// at once: grids of at most this many blocks run in a single wave.
+template <typename K>
+inline int resident_blocks(K kernel, size_t smem) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, SCGAL_BS, smem);
+    return (per > 0 ? per : 1) * (sms > 0 ? sms : 1);
+}
 #define SCGAL_RMAX 32         // largest sketch size R
 
 namespace scgal {
@@ -121,9 +132,11 @@ __device__ __forceinline__ void from_f64(double& o, double a) { o = a; }
 // 2-D grids, blocks numbered blockIdx.y * gridDim.x + blockIdx.x).
 // Returns true in exactly one block (the last to arrive); there tot[0..NV)
 // (shared memory) holds the grid totals for every thread after the call.
-template <int NV>
-__device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* __restrict__ partials,
+template <int NV, typename WT = double>
+__device__ __forceinline__ bool grid_reduce(WT (&v)[NV], double* __restrict__ partials,
                                             unsigned* __restrict__ ticket, double* tot) {
+    // WT: type of the warp-level sums (float on the FP32 path: FP64 arithmetic is
+    // scarce on GB300); warp, block and grid totals are then added in FP64.
     __shared__ double red[SCGAL_BS / 32][NV];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -131,10 +144,10 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* __restrict_
     const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        double x = v[k];
+        WT x = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[wid][k] = x;
+        if (lane == 0) red[wid][k] = (double)x;
     }
     __syncthreads();
     if (threadIdx.x < NV) {
@@ -142,8 +155,8 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* __restrict_
 #pragma unroll
         for (int w = 0; w < SCGAL_BS / 32; ++w) s += red[w][threadIdx.x];
         partials[(size_t)threadIdx.x * nblk + bid] = s;
+        __threadfence();   // this block's partials are visible before its ticket
     }
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(ticket, 1u);
@@ -173,10 +186,10 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* __restrict_
     return true;
 }
 
-template <int NV>
-__device__ __forceinline__ bool grid_reduce_2d(double (&v)[NV], double* __restrict__ partials,
+template <int NV, typename WT = double>
+__device__ __forceinline__ bool grid_reduce_2d(WT (&v)[NV], double* __restrict__ partials,
                                                unsigned* __restrict__ ticket, double* tot) {
-    return grid_reduce<NV>(v, partials, ticket, tot);
+    return grid_reduce<NV, WT>(v, partials, ticket, tot);
 }
 
 }  // namespace scgal

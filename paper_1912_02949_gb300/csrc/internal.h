@@ -118,7 +118,7 @@ struct scgal_ctx {
     double alpha_orig = 0, normC = 0, normA = 0;
     int trace_correct = 1;
     int spmv_group = 8;
-    int grid_elem = 1, grid_spmv = 1;
+    int grid_elem = 1, grid_spmv = 1, grid_ritz = 1;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream the iteration graphs are captured on
     bool own_stream = false;
@@ -159,6 +159,10 @@ template <typename V> void launch_tridiag(const KP<V>& p, int q, cudaStream_t s)
 template <typename V> void launch_ritz(const KP<V>& p, int grid, cudaStream_t s);
 template <typename V> void launch_gen_omega(const KP<V>& p, int grid, cudaStream_t s);
 template <typename V> void launch_start_only(const KP<V>& p, int grid, long long t, cudaStream_t s);
+// launch-shape queries (call before any stream capture)
+template <typename V> int ritz_resident(const KP<V>& p);
+template <typename V> void prepare_lanczos_shapes();
+template <typename V> void prepare_maxcut_shapes();
 
 // creation, rounding and reconstruction helpers
 int maxcut_check_and_scan(const int* row_ptr, const int* col, const double* w, int n, long long nnz, int* flags,

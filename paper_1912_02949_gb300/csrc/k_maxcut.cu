@@ -3,69 +3,124 @@
 // D-matvec.  D = C' + A'*(w) with C' = -sC L / 4 and A'* w = sA diag(w), so
 //     (D x)_r = dvec_r x_r + coff * sum_{j in N(r)} w_rj x_j,
 //     dvec_r  = -sC deg_r / 4 + sA w_r,     coff = sC / 4,
-// one CSR pass with a group of G lanes per row (G chosen from the average
-// degree); rows are taken warp-aligned so every shuffle has all 32 lanes.
+// one CSR pass, a warp per chunk of 32 rows (spmv_chunks).
 // Weights: unit (no value array), +/-1 (sign packed in bit 31 of the column
 // index: 4 bytes per stored entry), or general (value array).
+#include <algorithm>
+
 #include "internal.h"
 
 namespace scgal {
 
-template <typename V, int G, int WK>
-__device__ __forceinline__ V spmv_rows(const KP<V>& p, const V* __restrict__ x, V* __restrict__ out,
-                                       const V* __restrict__ diag) {
-    constexpr int GW = 32 / G;
+// One warp per chunk of 32 consecutive rows: lane l loads row_ptr[r0+l] and
+// row_ptr[r0+l+1] (one coalesced load each), then the warp streams the chunk's
+// nonzeros in coalesced passes -- all column loads of a pass first, then all
+// gathers of x -- and parks the products in shared memory; each lane then adds
+// up its own row.  Three dependent memory round trips per 32 rows instead of per
+// row.  Chunks with more nonzeros than the per-warp buffer are done in pieces.
+template <typename V, int WK>
+__device__ __forceinline__ V spmv_chunks(const KP<V>& p, const V* __restrict__ x, V* __restrict__ out,
+                                         const V* __restrict__ diag) {
+    constexpr int WPB = SCGAL_BS / 32;
+    constexpr int CAP = 24576 / (WPB * (int)sizeof(V));   // products per warp per piece
+    constexpr int U = 6;                                   // passes of 32 issued back to back
+    __shared__ V prod[WPB][CAP];
     const int lane = threadIdx.x & 31;
-    const int lg = lane & (G - 1);
-    const int gid = lane / G;
+    V* pw = prod[threadIdx.x >> 5];
+    const int n = p.c.n;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const V coff = (V)p.c.coff;
-    const int n = p.c.n;
     V dot = 0;
-    for (long long rb = warp * GW; rb < n; rb += nwarps * GW) {
-        const int r = (int)rb + gid;
-        const bool act = r < n;
-        int b = 0, e = 0;
-        if (act) {
-            b = __ldg(p.row_ptr + r);
-            e = __ldg(p.row_ptr + r + 1);
+    long long r0 = warp * 32;
+    // row data of the first chunk; later chunks are prefetched one chunk ahead
+    int rs = 0, re = 0;
+    V xr = 0, dr = 0;
+    if (r0 < n) {
+        const int r = (int)r0 + lane;
+        rs = __ldg(p.row_ptr + min(r, n));
+        re = __ldg(p.row_ptr + min(r + 1, n));
+        if (r < n) {
+            xr = x[r];
+            dr = diag[r];
         }
-        V s = 0;
-        for (int j = b + lg; j < e; j += G) {
-            const int cj = __ldg(p.col + j);
-            if constexpr (WK == W_PM1) {
-                const V xv = __ldg(x + (cj & 0x7fffffff));
-                s += (cj < 0) ? -xv : xv;
-            } else if constexpr (WK == W_UNIT) {
-                s += __ldg(x + cj);
-            } else {
-                s = fma(__ldg(p.val + j), __ldg(x + cj), s);
+    }
+    for (; r0 < n; r0 += nwarps * 32) {
+        const int r = (int)r0 + lane;
+        const bool act = r < n;
+        const int base = __shfl_sync(0xffffffffu, rs, 0);
+        const int end = __shfl_sync(0xffffffffu, re, 31);
+        // prefetch the next chunk's row pointers and own-row values
+        const long long r0n = r0 + nwarps * 32;
+        int rs_n = 0, re_n = 0;
+        V xr_n = 0, dr_n = 0;
+        if (r0n < n) {
+            const int rn = (int)r0n + lane;
+            rs_n = __ldg(p.row_ptr + min(rn, n));
+            re_n = __ldg(p.row_ptr + min(rn + 1, n));
+            if (rn < n) {
+                xr_n = x[rn];
+                dr_n = diag[rn];
             }
         }
+        V acc = 0;
+        for (int pb = base; pb < end; pb += CAP) {
+            const int pe = min(end, pb + CAP);
+            for (int q0 = pb; q0 < pe; q0 += 32 * U) {
+                int cj[U];
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (act && lg == 0) {
-            const V xr = x[r];
-            const V yr = fma(diag[r], xr, coff * s);
+                for (int u = 0; u < U; ++u) {
+                    const int e = q0 + u * 32 + lane;
+                    cj[u] = (e < pe) ? __ldg(p.col + e) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = q0 + u * 32 + lane;
+                    if (e < pe) {
+                        V xv;
+                        if constexpr (WK == W_PM1) {
+                            xv = __ldg(x + (cj[u] & 0x7fffffff));
+                            if (cj[u] < 0) xv = -xv;
+                        } else if constexpr (WK == W_UNIT) {
+                            xv = __ldg(x + cj[u]);
+                        } else {
+                            xv = __ldg(p.val + e) * __ldg(x + cj[u]);
+                        }
+                        pw[e - pb] = xv;
+                    }
+                }
+            }
+            __syncwarp();
+            const int a = max(rs, pb), b = min(re, pe);
+            for (int e = a; e < b; ++e) acc += pw[e - pb];
+            __syncwarp();
+        }
+        if (act) {
+            const V yr = fma(dr, xr, coff * acc);
             if (out) out[r] = yr;
             dot = fma(xr, yr, dot);
         }
+        rs = rs_n;
+        re = re_n;
+        xr = xr_n;
+        dr = dr_n;
     }
     return dot;
 }
 
 // Lanczos step i: Y = D W_i and omega_i = s_i^2 <W_i, Y>.
-template <typename V, int G, int WK>
+// Runs speculatively: it writes only per-iteration scratch (ybuf) until its last
+// block, which records omega_i only if the iteration is live (no convergence,
+// no breakdown) -- so no warp waits on the flags before its first load.
+template <typename V, int WK>
 __global__ void __launch_bounds__(SCGAL_BS) k_spmv_step(KP<V> p, int i) {
     DevScalars* sc = p.sc;
-    if (sc->converged || sc->stop) return;
     const V* x = p.basis + (size_t)i * p.ldb;
-    const V dot = spmv_rows<V, G, WK>(p, x, p.ybuf, p.dvec);
-    double v[1] = {(double)dot};
+    const V dot = spmv_chunks<V, WK>(p, x, p.ybuf, p.dvec);
+    V v[1] = {dot};
     __shared__ double tot[1];
-    if (grid_reduce<1>(v, p.partials, p.ticket, tot)) {
-        if (threadIdx.x == 0) {
+    if (grid_reduce<1, V>(v, p.partials, p.ticket, tot)) {
+        if (threadIdx.x == 0 && !sc->converged && !sc->stop) {
             const double si = p.sv[i];
             const double om = si * si * tot[0];
             if (!isfinite(om)) {
@@ -82,12 +137,12 @@ __global__ void __launch_bounds__(SCGAL_BS) k_spmv_step(KP<V> p, int i) {
 // updates of Eq. 6.2 z <- (1-eta) z + eta A(alpha v v*), S <- (1-eta) S +
 // eta alpha v (v* Omega) with v = vbuf / ||vbuf||, the objective and trace
 // updates (Section 6.2.2, Eq. B.2), and the dual step size of Eq. 6.4.
-template <typename V, int G, int WK>
+template <typename V, int WK>
 __global__ void __launch_bounds__(SCGAL_BS) k_vcv_update(KP<V> p) {
     DevScalars* sc = p.sc;
     if (sc->converged) return;
     const V* __restrict__ v = p.vbuf;
-    const V vcv = spmv_rows<V, G, WK>(p, v, nullptr, p.cdiag);
+    const V vcv = spmv_chunks<V, WK>(p, v, nullptr, p.cdiag);
     const double eta = sc->eta, nv2 = sc->nv2;
     const int take = sc->take_h;
     const int n = p.c.n, R = p.c.R;
@@ -111,15 +166,30 @@ __global__ void __launch_bounds__(SCGAL_BS) k_vcv_update(KP<V> p) {
             a_yy = fma(yi, yi, a_yy);
         }
     }
+    // sketch: S <- (1-eta) S + eta alpha v (v* Omega) / ||v||^2, 16-byte groups of the flat n x R array
+    constexpr int W = 16 / sizeof(V);
+    struct alignas(16) SV { V v[W]; };
     const long long nR = (long long)n * R;
-    for (long long k = gt; k < nR; k += st) {
-        const int e = (int)(k / R);
-        const int c = (int)(k - (long long)e * R);
-        p.S[k] = fma(om1, p.S[k], sfac * v[e] * rr[c]);
+    const long long nRv = nR / W;
+    for (long long kq = gt; kq < nRv; kq += st) {
+        SV sv = reinterpret_cast<const SV*>(p.S)[kq];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const long long kk = kq * W + j;
+            const int e = (int)(kk / R);
+            const int c = (int)(kk - (long long)e * R);
+            sv.v[j] = fma(om1, sv.v[j], sfac * v[e] * rr[c]);
+        }
+        reinterpret_cast<SV*>(p.S)[kq] = sv;
+    }
+    for (long long kk = nRv * W + gt; kk < nR; kk += st) {
+        const int e = (int)(kk / R);
+        const int c = (int)(kk - (long long)e * R);
+        p.S[kk] = fma(om1, p.S[kk], sfac * v[e] * rr[c]);
     }
     double red[4] = {(double)vcv, a_nzb, a_yzb, a_yy};
     __shared__ double tot[4];
-    if (grid_reduce<4>(red, p.partials, p.ticket, tot)) {
+    if (grid_reduce<4, double>(red, p.partials, p.ticket, tot)) {
         if (threadIdx.x == 0) {
             const Consts& c = p.c;
             const double vcvn = tot[0] / nv2;
@@ -143,9 +213,9 @@ __global__ void __launch_bounds__(SCGAL_BS) k_vcv_update(KP<V> p) {
     }
 }
 
-template <typename V, int G, int WK>
+template <typename V, int WK>
 __global__ void __launch_bounds__(SCGAL_BS) k_apply_D(KP<V> p, const V* x, V* out, const V* diag) {
-    (void)spmv_rows<V, G, WK>(p, x, out, diag);
+    (void)spmv_chunks<V, WK>(p, x, out, diag);
 }
 
 template <typename V>
@@ -155,31 +225,40 @@ __global__ void k_dvec_from_w(KP<V> p, const double* w) {
 }
 
 // ---------------------------------------------------------------------------
-template <typename V, int WK>
-static void spmv_dispatch_group(int group, const KP<V>& p, int grid, cudaStream_t s, int which, int i,
-                                const V* x, V* out, const V* diag) {
-#define GO(G)                                                                                  \
-    do {                                                                                       \
-        if (which == 0) k_spmv_step<V, G, WK><<<grid, SCGAL_BS, 0, s>>>(p, i);               \
-        else if (which == 1) k_vcv_update<V, G, WK><<<grid, SCGAL_BS, 0, s>>>(p);              \
-        else k_apply_D<V, G, WK><<<grid, SCGAL_BS, 0, s>>>(p, x, out, diag);                   \
-    } while (0)
-    switch (group) {
-        case 2: GO(2); break;
-        case 4: GO(4); break;
-        case 8: GO(8); break;
-        case 16: GO(16); break;
-        default: GO(32); break;
+// Blocks resident at once for each D-matvec kernel (queried once, before any
+// stream capture, by prepare_maxcut_shapes); grids never exceed one wave.
+template <typename V, int WK> int resident_spmv(int which) {
+    static const int r[3] = {resident_blocks(k_spmv_step<V, WK>, 0), resident_blocks(k_vcv_update<V, WK>, 0),
+                             resident_blocks(k_apply_D<V, WK>, 0)};
+    return r[which];
+}
+
+template <typename V> void prepare_maxcut_shapes() {
+    for (int w = 0; w < 3; ++w) {
+        (void)resident_spmv<V, W_UNIT>(w);
+        (void)resident_spmv<V, W_PM1>(w);
+        (void)resident_spmv<V, W_REAL>(w);
     }
-#undef GO
+}
+template void prepare_maxcut_shapes<float>();
+template void prepare_maxcut_shapes<double>();
+
+template <typename V, int WK>
+static void spmv_dispatch_kind(const KP<V>& p, int grid, cudaStream_t s, int which, int i, const V* x, V* out,
+                               const V* diag) {
+    const int g = std::min(grid, resident_spmv<V, WK>(which));   // one wave, grid-stride loops
+    if (which == 0) k_spmv_step<V, WK><<<g, SCGAL_BS, 0, s>>>(p, i);
+    else if (which == 1) k_vcv_update<V, WK><<<g, SCGAL_BS, 0, s>>>(p);
+    else k_apply_D<V, WK><<<g, SCGAL_BS, 0, s>>>(p, x, out, diag);
 }
 
 template <typename V>
 static void spmv_dispatch(const KP<V>& p, int grid, int group, cudaStream_t s, int which, int i,
                           const V* x = nullptr, V* out = nullptr, const V* diag = nullptr) {
-    if (p.c.wkind == W_PM1) spmv_dispatch_group<V, W_PM1>(group, p, grid, s, which, i, x, out, diag);
-    else if (p.c.wkind == W_UNIT) spmv_dispatch_group<V, W_UNIT>(group, p, grid, s, which, i, x, out, diag);
-    else spmv_dispatch_group<V, W_REAL>(group, p, grid, s, which, i, x, out, diag);
+    (void)group;
+    if (p.c.wkind == W_PM1) spmv_dispatch_kind<V, W_PM1>(p, grid, s, which, i, x, out, diag);
+    else if (p.c.wkind == W_UNIT) spmv_dispatch_kind<V, W_UNIT>(p, grid, s, which, i, x, out, diag);
+    else spmv_dispatch_kind<V, W_REAL>(p, grid, s, which, i, x, out, diag);
 }
 
 template <typename V> void launch_spmv_step(const KP<V>& p, int grid, int group, int i, cudaStream_t s) {
