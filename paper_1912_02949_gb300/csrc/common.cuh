@@ -18,6 +18,28 @@
 
 #define SCGAL_BS 256          // threads per block of every reduction kernel
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// while its predecessor in the stream drains; before touching anything the
+// predecessor writes it calls pdl_wait(), which returns once the predecessor has
+// completed and its writes are visible (immediately if there is none).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Blocks of `kernel` (SCGAL_BS threads, `smem` dynamic bytes) that fit on the GPU
 // at once: grids of at most this many blocks run in a single wave.
 template <typename K>
@@ -184,6 +206,44 @@ __device__ __forceinline__ bool grid_reduce(WT (&v)[NV], double* __restrict__ pa
     if (threadIdx.x == 0) *ticket = 0u;
     __syncthreads();
     return true;
+}
+
+// Block-level sum of one value into `out` (thread 0 writes), fixed order.
+template <typename WT>
+__device__ __forceinline__ void block_sum_to(WT v, double* out) {
+    __shared__ double red[SCGAL_BS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid] = (double)v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < SCGAL_BS / 32; ++w) s += red[w];
+        *out = s;
+    }
+}
+
+// Block-wide fixed-order sum of x[0..m) (every thread receives the total).
+__device__ __forceinline__ double block_sum_array(const double* x, int m) {
+    __shared__ double red[SCGAL_BS / 32];
+    __shared__ double res;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < m; b += SCGAL_BS) s += __ldcg(x + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < SCGAL_BS / 32; ++w) t += red[w];
+        res = t;
+    }
+    __syncthreads();
+    return res;
 }
 
 template <int NV, typename WT = double>

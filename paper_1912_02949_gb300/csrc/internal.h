@@ -100,7 +100,44 @@ struct KP {
     double* sv;         // 1 / ||w_i|| of raw basis vector i
     double* coef;       // Ritz coefficients u_j * sv_j
     scgal_stats* hist;
+    double* upart;      // per-block partial ||W_{i+1}||^2 of the last Lanczos update
+    int nupd;           // blocks of the Lanczos update kernel (entries of upart)
 };
+
+// Last block of a Lanczos D-matvec step i (all threads of the block call it):
+// rho_{i-1} from the previous update's per-block partials, the breakdown test
+// of Alg. 4.1 (exact rho == 0), the scale s_i = 1 / rho_{i-1}, and
+// omega_i = s_i^2 <W_i, D W_i>.  Nothing is recorded once the iteration has
+// converged or broken down.
+template <typename V>
+__device__ __forceinline__ void finish_lanczos_step(const KP<V>& p, int i, double dot) {
+    DevScalars* sc = p.sc;
+    const double rr = (i > 0) ? block_sum_array(p.upart, p.nupd) : 0.0;
+    if (threadIdx.x != 0 || sc->converged || sc->stop) return;
+    if (i > 0) {
+        const double rho = sqrt(rr);
+        if (rho == 0.0) {           // invariant subspace found: T is i x i
+            sc->stop = 1;
+            return;
+        }
+        if (!isfinite(rho)) {
+            sc->stop = 1;
+            sc->err = SCGAL_ENUMERIC;
+            sc->converged = 1;
+            return;
+        }
+        p.rh[i - 1] = rho;
+        p.sv[i] = 1.0 / rho;
+    }
+    const double si = p.sv[i];
+    const double om = si * si * dot;
+    if (!isfinite(om)) {
+        sc->err = SCGAL_ENUMERIC;
+        sc->converged = 1;
+    }
+    p.om[i] = om;
+    sc->k = i + 1;
+}
 
 }  // namespace scgal
 
@@ -161,6 +198,7 @@ template <typename V> void launch_gen_omega(const KP<V>& p, int grid, cudaStream
 template <typename V> void launch_start_only(const KP<V>& p, int grid, long long t, cudaStream_t s);
 // launch-shape queries (call before any stream capture)
 template <typename V> int ritz_resident(const KP<V>& p);
+template <typename V> int update_grid(int grid);
 template <typename V> void prepare_lanczos_shapes();
 template <typename V> void prepare_maxcut_shapes();
 

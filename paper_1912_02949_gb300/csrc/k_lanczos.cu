@@ -27,6 +27,7 @@ template <typename V>
 __global__ void __launch_bounds__(SCGAL_BS) k_dual_start(KP<V> p, int do_dual) {
     typedef typename VT<V>::R Rt;
     DevScalars* sc = p.sc;
+    pdl_wait();
     if (sc->converged) return;
     const long long t1 = sc->t + 1;
     const double gamma = do_dual ? sc->gamma : 0.0;
@@ -96,16 +97,16 @@ __global__ void __launch_bounds__(SCGAL_BS) k_dual_start(KP<V> p, int do_dual) {
 
 // ---------------------------------------------------------------------------
 // The update is linear with real coefficients, so it runs on the real view of
-// the vectors (2n reals for complex ones) with 16-byte loads.
+// the vectors (2n reals for complex ones) with 16-byte loads.  It has no grid
+// reduction: each block leaves its partial ||W_{i+1}||^2 in upart, and the next
+// D-matvec step adds them up (finish_lanczos_step).  Speculative like that step:
+// after a breakdown sv[i] may be stale, and the row it writes is never read.
 template <typename V>
 __global__ void __launch_bounds__(SCGAL_BS, 8) k_lanczos_update(KP<V> p, int i) {
     typedef typename VT<V>::R Rt;
     constexpr int W = 16 / sizeof(Rt);
     struct alignas(16) RV { Rt v[W]; };
-    DevScalars* sc = p.sc;
-    // speculative like the D-matvec step: only scratch is written before the last
-    // block checks the flags (after a breakdown sv[i] may be stale; the row it
-    // writes is then never read)
+    pdl_wait();
     const double si = p.sv[i];
     const Rt a = (Rt)si;
     const Rt b = (Rt)(-p.om[i] * si);
@@ -145,23 +146,7 @@ __global__ void __launch_bounds__(SCGAL_BS, 8) k_lanczos_update(KP<V> p, int i) 
         Wn[k] = w;
         acc += w * w;
     }
-    Rt v[1] = {acc};
-    __shared__ double tot[1];
-    if (grid_reduce<1, Rt>(v, p.partials, p.ticket, tot)) {
-        if (threadIdx.x == 0 && !sc->converged && !sc->stop) {
-            const double rho = sqrt(tot[0]);
-            if (rho == 0.0) {
-                sc->stop = 1;                 // invariant subspace found (Alg. 4.1)
-            } else if (!isfinite(rho)) {
-                sc->stop = 1;
-                sc->err = SCGAL_ENUMERIC;
-                sc->converged = 1;
-            } else {
-                p.rh[i] = rho;
-                p.sv[i + 1] = 1.0 / rho;
-            }
-        }
-    }
+    block_sum_to<Rt>(acc, p.upart + blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -184,6 +169,7 @@ __global__ void __launch_bounds__(SCGAL_BS, 8) k_lanczos_update(KP<V> p, int i) 
 template <typename V>
 __global__ void __launch_bounds__(SCGAL_BS) k_tridiag(KP<V> p, int q) {
     DevScalars* sc = p.sc;
+    pdl_wait();
     if (sc->converged) return;
     extern __shared__ double smt[];
     const int k = sc->k;
@@ -434,6 +420,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ritz(KP<V> p) {
     constexpr int EPT = W / CF;
     struct alignas(16) RV { Rt v[W]; };
     DevScalars* sc = p.sc;
+    pdl_wait();
     if (sc->converged) return;
     extern __shared__ double smr[];
     Rt* cf = reinterpret_cast<Rt*>(smr);
@@ -621,21 +608,24 @@ template <typename V> void prepare_lanczos_shapes() {
 }
 
 template <typename V> void launch_dual_start(const KP<V>& p, int grid, int do_dual, cudaStream_t s) {
-    k_dual_start<V><<<std::min(grid, resident_dual<V>()), SCGAL_BS, 0, s>>>(p, do_dual);
+    launch_pdl(k_dual_start<V>, std::min(grid, resident_dual<V>()), SCGAL_BS, 0, s, p, do_dual);
 }
+template <typename V> int update_grid(int grid) { return std::min(grid, resident_update<V>()); }
 template <typename V> void launch_lanczos_update(const KP<V>& p, int grid, int i, cudaStream_t s) {
-    k_lanczos_update<V><<<std::min(grid, resident_update<V>()), SCGAL_BS, 0, s>>>(p, i);
+    // the grid must be the one p.nupd was sized for: the next step reads nupd partials
+    (void)grid;
+    launch_pdl(k_lanczos_update<V>, p.nupd, SCGAL_BS, 0, s, p, i);
 }
 template <typename V> void launch_tridiag(const KP<V>& p, int q, cudaStream_t s) {
-    k_tridiag<V><<<1, SCGAL_BS, 5 * (size_t)(q + 1) * sizeof(double), s>>>(p, q);   // 4 double + 2 float arrays
+    launch_pdl(k_tridiag<V>, 1, SCGAL_BS, 5 * (size_t)(q + 1) * sizeof(double), s, p, q);   // 4 double + 2 float arrays
 }
 template <typename V> void launch_ritz(const KP<V>& p, int grid, cudaStream_t s) {
     const size_t sm = sizeof(double) * (size_t)(p.c.qmax + 1);  // Ritz coefficients, k <= qmax
     // the caller caps grid at ritz_resident() (one wave)
-    if (p.c.R <= 4) k_ritz<V, 4><<<grid, SCGAL_BS, sm, s>>>(p);
-    else if (p.c.R <= 8) k_ritz<V, 8><<<grid, SCGAL_BS, sm, s>>>(p);
-    else if (p.c.R <= 16) k_ritz<V, 16><<<grid, SCGAL_BS, sm, s>>>(p);
-    else k_ritz<V, 32><<<grid, SCGAL_BS, sm, s>>>(p);
+    if (p.c.R <= 4) launch_pdl(k_ritz<V, 4>, grid, SCGAL_BS, sm, s, p);
+    else if (p.c.R <= 8) launch_pdl(k_ritz<V, 8>, grid, SCGAL_BS, sm, s, p);
+    else if (p.c.R <= 16) launch_pdl(k_ritz<V, 16>, grid, SCGAL_BS, sm, s, p);
+    else launch_pdl(k_ritz<V, 32>, grid, SCGAL_BS, sm, s, p);
 }
 template <typename V> void launch_gen_omega(const KP<V>& p, int grid, cudaStream_t s) {
     k_gen_omega<V><<<grid, SCGAL_BS, 0, s>>>(p);
@@ -649,6 +639,7 @@ template <typename V> void launch_gen_omega(const KP<V>& p, int grid, cudaStream
     template void launch_gen_omega<V>(const KP<V>&, int, cudaStream_t);             \
     template void launch_start_only<V>(const KP<V>&, int, long long, cudaStream_t);  \
     template int ritz_resident<V>(const KP<V>&);                                      \
+    template int update_grid<V>(int);                                                  \
     template void prepare_lanczos_shapes<V>();
 INST(float)
 INST(double)

@@ -33,13 +33,19 @@ __device__ __forceinline__ V spmv_chunks(const KP<V>& p, const V* __restrict__ x
     const V coff = (V)p.c.coff;
     V dot = 0;
     long long r0 = warp * 32;
-    // row data of the first chunk; later chunks are prefetched one chunk ahead
+    // row data of the first chunk; later chunks are prefetched one chunk ahead.
+    // The row pointers are static, so they are read before waiting for the
+    // previous kernel (whose output x is).
     int rs = 0, re = 0;
     V xr = 0, dr = 0;
     if (r0 < n) {
         const int r = (int)r0 + lane;
         rs = __ldg(p.row_ptr + min(r, n));
         re = __ldg(p.row_ptr + min(r + 1, n));
+    }
+    pdl_wait();
+    if (r0 < n) {
+        const int r = (int)r0 + lane;
         if (r < n) {
             xr = x[r];
             dr = diag[r];
@@ -110,27 +116,15 @@ __device__ __forceinline__ V spmv_chunks(const KP<V>& p, const V* __restrict__ x
 
 // Lanczos step i: Y = D W_i and omega_i = s_i^2 <W_i, Y>.
 // Runs speculatively: it writes only per-iteration scratch (ybuf) until its last
-// block, which records omega_i only if the iteration is live (no convergence,
-// no breakdown) -- so no warp waits on the flags before its first load.
+// block, which records omega_i (and rho_{i-1} from the previous update) only if
+// the iteration is live -- so no warp waits on the flags before its first load.
 template <typename V, int WK>
 __global__ void __launch_bounds__(SCGAL_BS) k_spmv_step(KP<V> p, int i) {
-    DevScalars* sc = p.sc;
     const V* x = p.basis + (size_t)i * p.ldb;
     const V dot = spmv_chunks<V, WK>(p, x, p.ybuf, p.dvec);
     V v[1] = {dot};
     __shared__ double tot[1];
-    if (grid_reduce<1, V>(v, p.partials, p.ticket, tot)) {
-        if (threadIdx.x == 0 && !sc->converged && !sc->stop) {
-            const double si = p.sv[i];
-            const double om = si * si * tot[0];
-            if (!isfinite(om)) {
-                sc->err = SCGAL_ENUMERIC;
-                sc->converged = 1;
-            }
-            p.om[i] = om;
-            sc->k = i + 1;
-        }
-    }
+    if (grid_reduce<1, V>(v, p.partials, p.ticket, tot)) finish_lanczos_step(p, i, tot[0]);
 }
 
 // After the Ritz vector: v* C v (primitive (1), one more CSR pass), the primal
@@ -140,6 +134,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_spmv_step(KP<V> p, int i) {
 template <typename V, int WK>
 __global__ void __launch_bounds__(SCGAL_BS) k_vcv_update(KP<V> p) {
     DevScalars* sc = p.sc;
+    pdl_wait();
     if (sc->converged) return;
     const V* __restrict__ v = p.vbuf;
     const V vcv = spmv_chunks<V, WK>(p, v, nullptr, p.cdiag);
@@ -247,8 +242,8 @@ template <typename V, int WK>
 static void spmv_dispatch_kind(const KP<V>& p, int grid, cudaStream_t s, int which, int i, const V* x, V* out,
                                const V* diag) {
     const int g = std::min(grid, resident_spmv<V, WK>(which));   // one wave, grid-stride loops
-    if (which == 0) k_spmv_step<V, WK><<<g, SCGAL_BS, 0, s>>>(p, i);
-    else if (which == 1) k_vcv_update<V, WK><<<g, SCGAL_BS, 0, s>>>(p);
+    if (which == 0) launch_pdl(k_spmv_step<V, WK>, g, SCGAL_BS, 0, s, p, i);
+    else if (which == 1) launch_pdl(k_vcv_update<V, WK>, g, SCGAL_BS, 0, s, p);
     else k_apply_D<V, WK><<<g, SCGAL_BS, 0, s>>>(p, x, out, diag);
 }
 

@@ -207,8 +207,6 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ph_p3(KP<V> p, const V* __restrict
     constexpr int MAXE = 16;   // elements per thread (n2 * TC <= 16 * SCGAL_BS)
     extern __shared__ unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
-    DevScalars* sc = p.sc;
-    if (DOT && (sc->converged || sc->stop)) return;
     const int n = p.c.n, n1 = p.n1, n2 = p.n2, TC = p.ph_tc, lg2 = p.log2, L = p.c.L;
     const int m1base = blockIdx.x * TC;
     const int g = blockIdx.y;
@@ -260,18 +258,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ph_p3(KP<V> p, const V* __restrict
     if constexpr (DOT) {
         double v[1] = {(double)dot};
         __shared__ double tot[1];
-        if (grid_reduce_2d<1>(v, p.partials, p.ticket, tot)) {
-            if (threadIdx.x == 0) {
-                const double si = p.sv[i];
-                const double om = si * si * tot[0];
-                if (!isfinite(om)) {
-                    sc->err = SCGAL_ENUMERIC;
-                    sc->converged = 1;
-                }
-                p.om[i] = om;
-                sc->k = i + 1;
-            }
-        }
+        if (grid_reduce_2d<1>(v, p.partials, p.ticket, tot)) finish_lanczos_step(p, i, tot[0]);
     }
 }
 
