@@ -84,6 +84,26 @@ def profiled_traffic():
         return None
 
 
+def replica_seed(rank: int) -> int:
+    """Each rank solves its own replica of the workload (its own random draws)."""
+    return SEED + rank
+
+
+def aggregate_ranks(local_ms: float, steps: int, T: int, world: int, device=None):
+    """Whole-job throughput over `world` replicas: the slowest rank's time (max
+    over ranks after a barrier) and every rank's T * steps iterations.
+    Returns (value in iter/s, max ms).  With world == 1 no process group is used."""
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.barrier()
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    return world * steps * T / (total_ms / 1000.0), total_ms
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -241,6 +261,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--T", type=int, default=T_DEFAULT)
+    ap.add_argument("--workload", default="er2p20", choices=["er2p20", "torus2p23", "er800"],
+                    help="MaxCut graph (default: the n=2^20 random graph the metric is quoted on)")
     ap.add_argument("--sample-iters", type=int, default=6)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -278,7 +300,7 @@ def main():
     S.load()
     T = args.T
 
-    g = W.config_graph("er2p20", seed=SEED)
+    g = W.config_graph(args.workload, seed=SEED)
     rp, col, val = g.csr()
     n, nnz = g.n, int(col.size)
     d_rp = torch.from_numpy(rp).to(dev)
@@ -289,7 +311,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def params(prec, tol=0.0):
-        return S.scgal_params_default(R=R, T_max=T, precision=prec, seed=SEED + rank, tol=tol, device=local)
+        return S.scgal_params_default(R=R, T_max=T, precision=prec, seed=replica_seed(rank), tol=tol, device=local)
 
     def solve(prec, host=False, tol=0.0, keep=False):
         """One full solve; returns (ms, last record, best cut, lambda, handle or None)."""
@@ -327,14 +349,7 @@ def main():
         if hh is not None:
             hist32 = hh
     clk = clocks.stop()
-    total_ms = sum(times)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.barrier()
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * args.steps * T / (total_ms / 1000.0)
+    value, total_ms = aggregate_ranks(sum(times), args.steps, T, world, dev)
 
     extra = {}
     # the plain FP64 GPU path on the same solve, and both paths to relative gap <= 1e-3
@@ -379,14 +394,16 @@ def main():
                 "bytes_per_launch": bytes_step, "ms_per_launch": kern["spmv_step"], "peak_source": peak_src}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "er2p20":
         cpu = cpu_baseline_entry(run_cpu_sample(args.sample_iters), T)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "n": n, "m": g.m, "nnz": nnz, "R": R,
+                "config": {"workload": WORKLOAD if args.workload == "er2p20" else f"maxcut_{args.workload}",
+                           "desc": WORKLOAD_DESC if args.workload == "er2p20" else f"MaxCut SDP on {args.workload}",
+                           "n": n, "m": g.m, "nnz": nnz, "R": R,
                            "T": T, "precision": "fp32 vectors/matvec/sketch, fp64 reductions and dual state",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": L2_NOTE, "spmv_lanes_per_row": info["spmv_group"]},

@@ -283,3 +283,30 @@ def test_full_size_er2p20_matvec_and_first_iterations(S):
         assert math.isclose(st["z"].sum(), st["tau"], rel_tol=(1e-5 if prec == 32 else 1e-12))
         assert math.isclose(st["tau"], 1.0, rel_tol=1e-12)      # every step took H = v v*: tr X' = 1
         h.close()
+
+
+def test_full_size_torus2p23_matvec_and_first_iteration(S):
+    """n = 2^23: 2048 x 4096 torus plus 10% long-range edges, +/-1 weights (the
+    largest MaxCut workload; basis and sketch resident on one GPU).  One D-matvec
+    against the oracle; the first iteration's z = A(v v*) = |v|^2 (eta_1 = 1)
+    against the oracle's ApproxMinEvec on the same start vector; then the exact
+    invariant sum(z) = tau = tr X' = 1 after a few more iterations."""
+    g = W.config_graph("torus2p23")
+    prob = MaxCutProblem(g.n, g.i, g.j, g.w)
+    h = _handle(S, g, 32, R=10, T_max=1000)
+    r = np.random.default_rng(2)
+    x = r.standard_normal(g.n)
+    w = 1e-4 * r.standard_normal(g.n)
+    assert _relerr(S.scgal_apply_D(h, x, w), prob.C_apply(x) + prob.Astar_apply(w, x)) <= TOL_MV[32]
+    S.scgal_step(h)
+    st = S.scgal_get_state(h)
+    w1 = -math.sqrt(2) * prob.b                       # y = z = 0 at t = 1
+    v1 = gaussian_vector(0, PURPOSE_LANCZOS, 1, 0, g.n, False)
+    _, v, _ = approx_min_evec(lambda u: prob.C_apply(u) + prob.Astar_apply(w1, u), v1, lanczos_steps(g.n, 1))
+    z_ref = (v / np.linalg.norm(v)) ** 2
+    assert _relerr(st["z"], z_ref) <= 1e-4
+    S.scgal_solve(h, 4)
+    st = S.scgal_get_state(h)
+    assert math.isclose(st["z"].sum(), st["tau"], rel_tol=1e-5)
+    assert math.isclose(st["tau"], 1.0, rel_tol=1e-12)
+    h.close()
