@@ -149,6 +149,15 @@ int setup_state(scgal_ctx* h) {
     ALLOC(h, p.coef, sizeof(double) * (h->qmax + 2));
     ALLOC(h, p.hist, sizeof(scgal_stats) * (size_t)hist_cap);
     ALLOC(h, p.upart, sizeof(double) * (size_t)gmax);
+    {
+        int* qt = nullptr;
+        ALLOC(h, qt, sizeof(int) * (size_t)h->prm.T_max);
+        std::vector<int> hq((size_t)h->prm.T_max);
+        for (int t = 1; t <= h->prm.T_max; ++t) hq[t - 1] = lanczos_q(t, n);
+        CUDA_TRY(h, cudaMemcpyAsync(qt, hq.data(), sizeof(int) * hq.size(), cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        p.qtab = qt;
+    }
     p.ldb = h->ldb;
     h->c.qmax = h->qmax;
     h->c.hist_cap = hist_cap;
@@ -930,6 +939,31 @@ int do_launch(scgal_ctx* h, long long T_end) {
 }
 
 }  // namespace
+
+const void* scgal::handle_params(const scgal_ctx* h) { return h->kp; }
+
+// After a batched launch: the host's view of the handle from the status the
+// kernel left (next t, convergence); the record of the last iteration only for
+// a finished solve.
+int scgal::batch_apply(scgal_ctx* h, const BatchStatus& st, scgal_stats* out, int* done) {
+    *done = 0;
+    if (h->sticky) return h->sticky;
+    DeviceGuard guard(h);
+    if (h->cplx || h->prec != 32) return SCGAL_EINVAL;
+    if (st.err) return set_err(h, st.err, "non-finite value in the iteration");
+    long long rec_t;
+    if (st.converged) {
+        h->converged_host = 1;
+        h->t_next = st.conv_t;
+        rec_t = st.conv_t;
+    } else {
+        h->t_next = st.t;                 // the batched kernel prepared iteration st.t
+        rec_t = st.t - 1;
+    }
+    *done = st.converged || h->t_next > h->prm.T_max;
+    if (*done && rec_t >= 1) return read_record<float>(h, rec_t, out);
+    return SCGAL_OK;
+}
 
 // Enqueue iterations t_next .. T_end without waiting (serving loop).
 int scgal::launch_iterations(scgal_ctx* h, long long T_end) {

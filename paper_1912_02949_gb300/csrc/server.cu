@@ -46,6 +46,8 @@ struct Slot {
     scgal_t h = nullptr;
     Request req;
     bool active = false;
+    bool batched = false;   // advanced by the batched kernel (else by the handle's graphs)
+    int variant = 0;        // batched kernel variant
 };
 
 // Device bytes of one FP32 solve (mirrors the handle's allocations, with margin).
@@ -60,7 +62,8 @@ size_t estimate_footprint(int n, long long nnz, const scgal_params& p) {
                    + 2.0 * vb * n * p.R                          // Omega, S
                    + 16.0 * n                                    // z, y
                    + 2.0 * 16.0 * n * p.R                        // reconstruction Y, U (FP64)
-                   + 56.0 * p.T_max + 8.0 * 65 * 1216 + 65536;   // history, partials, scalars
+                   + 60.0 * p.T_max + 8.0 * 65 * 1216 + 65536    // history, q table, partials, scalars
+                   + 8.0 * nnz + 24.0 * n;                       // sliced layout of the batched engine
     return (size_t)(bytes * 1.15);
 }
 
@@ -80,8 +83,54 @@ struct scgal_server {
     size_t in_use = 0, peak = 0;
     long long submitted = 0, admitted = 0, completed = 0, rejected = 0;
     int active = 0;
-    static constexpr int CHUNK = 8;          // iterations per slot per round
+    static constexpr int CHUNK = 8;          // iterations per graph-path slot per round
+    static constexpr unsigned long long BATCH_BUDGET_NS = 10000000ull;   // batched launch time per round
     static constexpr size_t QUEUE_MAX = 1 << 16;
+    // batched engine state (device arrays owned by the worker thread)
+    cudaStream_t bstream = nullptr;
+    char* d_slots = nullptr;
+    int* d_active = nullptr;
+    int* d_ctl = nullptr;
+    scgal::BatchLaunch* blaunch = nullptr;
+    scgal::BatchStatus* d_status = nullptr;
+    scgal::BatchStatus* h_status = nullptr;   // pinned
+    std::vector<int> h_active;
+    std::vector<unsigned char> slot_desc;     // host copy of one slot descriptor
+    long long rounds = 0;
+
+    bool init_batch() {
+        if (bstream) return true;
+        if (cudaStreamCreateWithFlags(&bstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMalloc(&d_slots, scgal::batch_slot_bytes() * (size_t)max_slots) != cudaSuccess ||
+            cudaMalloc(&d_active, sizeof(int) * (size_t)max_slots) != cudaSuccess ||
+            cudaMalloc(&d_ctl, sizeof(int) * scgal::BATCH_CTL_INTS) != cudaSuccess ||
+            cudaMalloc(&d_status, sizeof(scgal::BatchStatus) * (size_t)max_slots) != cudaSuccess ||
+            cudaMallocHost(&h_status, sizeof(scgal::BatchStatus) * (size_t)max_slots) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        slot_desc.resize(scgal::batch_slot_bytes());
+        blaunch = scgal::batch_launch_create();
+        return blaunch != nullptr;
+    }
+
+    void free_batch() {
+        if (bstream) cudaStreamSynchronize(bstream);
+        scgal::batch_launch_destroy(blaunch);
+        blaunch = nullptr;
+        if (d_slots) cudaFree(d_slots);
+        if (d_active) cudaFree(d_active);
+        if (d_ctl) cudaFree(d_ctl);
+        if (d_status) cudaFree(d_status);
+        if (h_status) cudaFreeHost(h_status);
+        if (bstream) cudaStreamDestroy(bstream);
+        bstream = nullptr;
+        d_slots = nullptr;
+        d_active = nullptr;
+        d_ctl = nullptr;
+        d_status = nullptr;
+        h_status = nullptr;
+    }
 
     void publish(Slot& s, int status, const scgal_stats* st) {
         scgal_result r;
@@ -136,7 +185,10 @@ struct scgal_server {
                     cv_done.notify_all();
                 }
                 if (active == 0 && queue.empty()) {
-                    if (stopping) return;
+                    if (stopping) {
+                        free_batch();
+                        return;
+                    }
                     cv_work.wait_for(lk, std::chrono::milliseconds(50));
                     continue;
                 }
@@ -169,6 +221,7 @@ struct scgal_server {
                     fresh.push_back(i);
                 }
             }
+            const bool batch_ok = init_batch();
             for (int i : fresh) {
                 Slot& s = slots[i];
                 s.req.t_admit = now_ms();
@@ -178,16 +231,61 @@ struct scgal_server {
                 if (rc) {
                     s.h = nullptr;
                     publish(s, rc, nullptr);
+                    continue;
                 }
+                // small FP32 instances join the batched engine (else, or if its set-up
+                // fails, they run on the handle's own graphs)
+                s.batched = batch_ok && scgal::batch_eligible(s.h) && !scgal::batch_prepare(s.h, slot_desc.data()) &&
+                            cudaMemcpy(d_slots + slot_desc.size() * (size_t)i, slot_desc.data(), slot_desc.size(),
+                                       cudaMemcpyHostToDevice) == cudaSuccess;
+                if (s.batched) s.variant = scgal::batch_variant(slot_desc.data());
             }
-            // 2. one chunk of every resident solve, all enqueued before any wait
+            // 2. one chunk of every resident solve, all enqueued before any wait:
+            //    small FP32 instances in one batched launch, the others on their own streams
             std::vector<int> live;
-            for (int i = 0; i < max_slots; ++i) {
+            std::vector<int> bvar[scgal::BATCH_NVAR];
+            h_active.clear();
+            ++rounds;
+            for (int j = 0; j < max_slots; ++j) {
+                const int i = (int)((j + rounds) % max_slots);   // rotating order: no slot always last
                 Slot& s = slots[i];
                 if (!s.active || !s.h) continue;
+                if (s.batched) {
+                    bvar[s.variant].push_back(i);
+                    continue;
+                }
                 const int rc = scgal::launch_iterations(s.h, s.h->t_next + CHUNK - 1);
                 if (rc) publish(s, rc, nullptr);
                 else live.push_back(i);
+            }
+            int counts[scgal::BATCH_NVAR];
+            for (int v = 0; v < scgal::BATCH_NVAR; ++v) {
+                counts[v] = (int)bvar[v].size();
+                h_active.insert(h_active.end(), bvar[v].begin(), bvar[v].end());
+            }
+            if (!h_active.empty()) {
+                int rc = cudaMemcpyAsync(d_active, h_active.data(), sizeof(int) * h_active.size(),
+                                         cudaMemcpyHostToDevice, bstream) == cudaSuccess ? SCGAL_OK : SCGAL_ECUDA;
+                if (!rc)
+                    rc = scgal::launch_batch(blaunch, d_slots, d_active, counts, d_ctl, 1 << 30, BATCH_BUDGET_NS,
+                                             d_status, bstream);
+                if (!rc && cudaMemcpyAsync(h_status, d_status, sizeof(scgal::BatchStatus) * (size_t)max_slots,
+                                           cudaMemcpyDeviceToHost, bstream) != cudaSuccess)
+                    rc = SCGAL_ECUDA;
+                if (!rc && cudaStreamSynchronize(bstream) != cudaSuccess) rc = SCGAL_ECUDA;
+                for (int i : h_active) {
+                    Slot& s = slots[i];
+                    if (rc) {
+                        publish(s, rc, nullptr);
+                        continue;
+                    }
+                    scgal_stats st;
+                    std::memset(&st, 0, sizeof(st));
+                    int done = 0;
+                    const int rr = scgal::batch_apply(s.h, h_status[i], &st, &done);
+                    if (rr) publish(s, rr, nullptr);
+                    else if (done) publish(s, h_status[i].converged ? SCGAL_OK : SCGAL_ENOTDONE, &st);
+                }
             }
             // 3. wait, retire
             for (int i : live) {
