@@ -263,6 +263,10 @@ typedef struct {
     int64_t submitted, admitted, completed, rejected;
     int32_t active, queued;
     int64_t device_bytes_in_use, device_bytes_peak;
+    int64_t rounds;         /* serving rounds run */
+    double  wait_ms;        /* worker time blocked on running rounds */
+    double  admit_ms;       /* worker time creating solves (set-up, graph layout) */
+    double  retire_ms;      /* worker time retiring solves (reconstruction, rounding, release) */
 } scgal_server_stats;
 
 /* hbm_budget: bytes the server may hold on the device (admission control);

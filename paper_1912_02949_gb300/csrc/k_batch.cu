@@ -140,7 +140,7 @@ template <bool NARROW, int WK>
 __device__ __forceinline__ float bs_matvec(const BatchSlot& B, const float* __restrict__ dg, const float* xs,
                                            float* yo) {
     using PT = typename Pair<NARROW>::T;
-    constexpr int SL = 4, U = (NARROW && WK != W_REAL) ? 4 : 2;   // pairs in flight within the register budget
+    constexpr int SL = 4, U = (NARROW && WK != W_REAL) ? 5 : 2;   // pairs in flight within the register budget
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = B.p.c.n, ns = B.nslices;
     const float coff = (float)B.p.c.coff;
@@ -244,17 +244,19 @@ __device__ __forceinline__ void b_lanczos(const BatchSlot& B, int q) {
         float* __restrict__ Wn = p.basis + (size_t)(i + 1) * ldb;
         float acc[1] = {0.f};
         for (int base = threadIdx.x; base < n; base += BT * U) {
-            float wm[U];
+            float wm[U], yy[U], xx[U];               // all loads before the stores they may alias
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int r = base + u * BT;
                 wm[u] = (r < n) ? Wm[r] : 0.f;
+                yy[u] = (r < n) ? yv[r] : 0.f;
+                xx[u] = (r < n) ? xs[r] : 0.f;
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int r = base + u * BT;
                 if (r < n) {
-                    const float w = fmaf(a, yv[r], fmaf(b, xs[r], c * wm[u]));
+                    const float w = fmaf(a, yy[u], fmaf(b, xx[u], c * wm[u]));
                     Wn[r] = w;
                     xs[r] = w;               // next step's vector, in place (each r has one owner)
                     acc[0] += w * w;

@@ -5,11 +5,15 @@
 //      request's estimated device footprint fits the remaining budget (the
 //      solve's z, y, sketch and Lanczos basis then stay on the device until it
 //      finishes);
-//   2. enqueues the next chunk of iterations of every resident solve, each on
-//      the solve's own stream, before waiting for any of them, so the solves'
-//      kernels overlap on the GPU;
-//   3. retires the solves that met their stopping rule (Eq. E.1) or their
-//      T_max: Nystrom reconstruction, rounding, result published for scgal_poll.
+//   2. enqueues the next stretch of every resident solve before waiting for
+//      any of them: small FP32 instances in the batched engine's persistent
+//      launches (one per kernel variant, each instance running until a time
+//      budget is spent), the others as chunks of iterations on their own streams;
+//   3. while those run, sets up the solves admitted in step 1 (they join the
+//      next round) and retires the solves that finished in the previous round
+//      (met the stopping rule of Eq. E.1 or T_max): Nystrom reconstruction,
+//      rounding, result published for scgal_poll, device memory released;
+//   4. waits for the round and marks the solves that finished in it.
 // A request that arrives while others are mid-solve joins at the next round.
 #include <chrono>
 #include <cmath>
@@ -48,6 +52,10 @@ struct Slot {
     bool active = false;
     bool batched = false;   // advanced by the batched kernel (else by the handle's graphs)
     int variant = 0;        // batched kernel variant
+    bool fin = false;       // finished; retired during the next round
+    int fin_status = 0;
+    bool fin_has_st = false;
+    scgal_stats fin_st{};
 };
 
 // Device bytes of one FP32 solve (mirrors the handle's allocations, with margin).
@@ -82,6 +90,8 @@ struct scgal_server {
     uint64_t next_id = 1;
     size_t in_use = 0, peak = 0;
     long long submitted = 0, admitted = 0, completed = 0, rejected = 0;
+    double wait_ms = 0, admit_ms = 0, retire_ms = 0;   // worker time per phase (guarded by mu)
+    long long rounds_done = 0;
     int active = 0;
     static constexpr int CHUNK = 8;          // iterations per graph-path slot per round
     static constexpr unsigned long long BATCH_BUDGET_NS = 10000000ull;   // batched launch time per round
@@ -130,6 +140,19 @@ struct scgal_server {
         d_ctl = nullptr;
         d_status = nullptr;
         h_status = nullptr;
+    }
+
+    // The solve in s ended (status; its last iteration record if st): retired later.
+    void finish(Slot& s, int status, const scgal_stats* st) {
+        s.fin = true;
+        s.fin_status = status;
+        s.fin_has_st = st != nullptr;
+        if (st) s.fin_st = *st;
+    }
+
+    void retire(Slot& s) {
+        s.fin = false;
+        publish(s, s.fin_status, s.fin_has_st ? &s.fin_st : nullptr);
     }
 
     void publish(Slot& s, int status, const scgal_stats* st) {
@@ -222,6 +245,42 @@ struct scgal_server {
                 }
             }
             const bool batch_ok = init_batch();
+            // 2. one stretch of every resident solve, all enqueued before any wait:
+            //    small FP32 instances in the batched engine, the others on their own streams
+            std::vector<int> live;
+            std::vector<int> bvar[scgal::BATCH_NVAR];
+            h_active.clear();
+            ++rounds;
+            for (int j = 0; j < max_slots; ++j) {
+                const int i = (int)((j + rounds) % max_slots);   // rotating order: no slot always last
+                Slot& s = slots[i];
+                if (!s.active || !s.h || s.fin) continue;
+                if (s.batched) {
+                    bvar[s.variant].push_back(i);
+                    continue;
+                }
+                const int rc = scgal::launch_iterations(s.h, s.h->t_next + CHUNK - 1);
+                if (rc) finish(s, rc, nullptr);
+                else live.push_back(i);
+            }
+            int counts[scgal::BATCH_NVAR];
+            for (int v = 0; v < scgal::BATCH_NVAR; ++v) {
+                counts[v] = (int)bvar[v].size();
+                h_active.insert(h_active.end(), bvar[v].begin(), bvar[v].end());
+            }
+            int brc = SCGAL_OK;
+            if (!h_active.empty()) {
+                brc = cudaMemcpyAsync(d_active, h_active.data(), sizeof(int) * h_active.size(),
+                                      cudaMemcpyHostToDevice, bstream) == cudaSuccess ? SCGAL_OK : SCGAL_ECUDA;
+                if (!brc)
+                    brc = scgal::launch_batch(blaunch, d_slots, d_active, counts, d_ctl, 1 << 30, BATCH_BUDGET_NS,
+                                              d_status, bstream);
+                if (!brc && cudaMemcpyAsync(h_status, d_status, sizeof(scgal::BatchStatus) * (size_t)max_slots,
+                                            cudaMemcpyDeviceToHost, bstream) != cudaSuccess)
+                    brc = SCGAL_ECUDA;
+            }
+            // 3. while the round runs: set up the new solves, retire the finished ones
+            double t0 = now_ms();
             for (int i : fresh) {
                 Slot& s = slots[i];
                 s.req.t_admit = now_ms();
@@ -230,7 +289,7 @@ struct scgal_server {
                                                    &s.req.prm, &s.h);
                 if (rc) {
                     s.h = nullptr;
-                    publish(s, rc, nullptr);
+                    finish(s, rc, nullptr);
                     continue;
                 }
                 // small FP32 instances join the batched engine (else, or if its set-up
@@ -240,64 +299,47 @@ struct scgal_server {
                                        cudaMemcpyHostToDevice) == cudaSuccess;
                 if (s.batched) s.variant = scgal::batch_variant(slot_desc.data());
             }
-            // 2. one chunk of every resident solve, all enqueued before any wait:
-            //    small FP32 instances in one batched launch, the others on their own streams
-            std::vector<int> live;
-            std::vector<int> bvar[scgal::BATCH_NVAR];
-            h_active.clear();
-            ++rounds;
-            for (int j = 0; j < max_slots; ++j) {
-                const int i = (int)((j + rounds) % max_slots);   // rotating order: no slot always last
+            double t1 = now_ms();
+            const double d_admit = t1 - t0;
+            for (int i = 0; i < max_slots; ++i) {
                 Slot& s = slots[i];
-                if (!s.active || !s.h) continue;
-                if (s.batched) {
-                    bvar[s.variant].push_back(i);
-                    continue;
-                }
-                const int rc = scgal::launch_iterations(s.h, s.h->t_next + CHUNK - 1);
-                if (rc) publish(s, rc, nullptr);
-                else live.push_back(i);
+                if (s.active && s.fin) retire(s);
             }
-            int counts[scgal::BATCH_NVAR];
-            for (int v = 0; v < scgal::BATCH_NVAR; ++v) {
-                counts[v] = (int)bvar[v].size();
-                h_active.insert(h_active.end(), bvar[v].begin(), bvar[v].end());
-            }
+            t0 = now_ms();
+            const double d_retire = t0 - t1;
+            // 4. wait for the round; mark the solves that finished in it
             if (!h_active.empty()) {
-                int rc = cudaMemcpyAsync(d_active, h_active.data(), sizeof(int) * h_active.size(),
-                                         cudaMemcpyHostToDevice, bstream) == cudaSuccess ? SCGAL_OK : SCGAL_ECUDA;
-                if (!rc)
-                    rc = scgal::launch_batch(blaunch, d_slots, d_active, counts, d_ctl, 1 << 30, BATCH_BUDGET_NS,
-                                             d_status, bstream);
-                if (!rc && cudaMemcpyAsync(h_status, d_status, sizeof(scgal::BatchStatus) * (size_t)max_slots,
-                                           cudaMemcpyDeviceToHost, bstream) != cudaSuccess)
-                    rc = SCGAL_ECUDA;
-                if (!rc && cudaStreamSynchronize(bstream) != cudaSuccess) rc = SCGAL_ECUDA;
+                if (!brc && cudaStreamSynchronize(bstream) != cudaSuccess) brc = SCGAL_ECUDA;
                 for (int i : h_active) {
                     Slot& s = slots[i];
-                    if (rc) {
-                        publish(s, rc, nullptr);
+                    if (brc) {
+                        finish(s, brc, nullptr);
                         continue;
                     }
                     scgal_stats st;
                     std::memset(&st, 0, sizeof(st));
                     int done = 0;
                     const int rr = scgal::batch_apply(s.h, h_status[i], &st, &done);
-                    if (rr) publish(s, rr, nullptr);
-                    else if (done) publish(s, h_status[i].converged ? SCGAL_OK : SCGAL_ENOTDONE, &st);
+                    if (rr) finish(s, rr, nullptr);
+                    else if (done) finish(s, h_status[i].converged ? SCGAL_OK : SCGAL_ENOTDONE, &st);
                 }
             }
-            // 3. wait, retire
             for (int i : live) {
                 Slot& s = slots[i];
                 scgal_stats st;
                 std::memset(&st, 0, sizeof(st));
                 int conv = 0;
                 const int rc = scgal::finish_iterations(s.h, &st, &conv);
-                if (rc) publish(s, rc, nullptr);
-                else if (conv) publish(s, SCGAL_OK, &st);
-                else if (s.h->t_next > s.req.prm.T_max) publish(s, SCGAL_ENOTDONE, &st);
+                if (rc) finish(s, rc, nullptr);
+                else if (conv) finish(s, SCGAL_OK, &st);
+                else if (s.h->t_next > s.req.prm.T_max) finish(s, SCGAL_ENOTDONE, &st);
             }
+            const double d_wait = now_ms() - t0;
+            std::lock_guard<std::mutex> lk(mu);
+            wait_ms += d_wait;
+            admit_ms += d_admit;
+            retire_ms += d_retire;
+            ++rounds_done;
         }
     }
 };
@@ -376,6 +418,10 @@ int scgal_server_get_stats(scgal_srv_t s, scgal_server_stats* out) {
     out->queued = (int32_t)s->queue.size();
     out->device_bytes_in_use = (int64_t)s->in_use;
     out->device_bytes_peak = (int64_t)s->peak;
+    out->rounds = s->rounds_done;
+    out->wait_ms = s->wait_ms;
+    out->admit_ms = s->admit_ms;
+    out->retire_ms = s->retire_ms;
     return SCGAL_OK;
 }
 

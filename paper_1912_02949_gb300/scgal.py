@@ -68,7 +68,8 @@ class scgal_result(Structure):
 class scgal_server_stats(Structure):
     _fields_ = [("submitted", c_int64), ("admitted", c_int64), ("completed", c_int64), ("rejected", c_int64),
                 ("active", c_int32), ("queued", c_int32), ("device_bytes_in_use", c_int64),
-                ("device_bytes_peak", c_int64)]
+                ("device_bytes_peak", c_int64), ("rounds", c_int64), ("wait_ms", c_double),
+                ("admit_ms", c_double), ("retire_ms", c_double)]
 
 
 # name -> (restype, argtypes), exactly the declarations of include/scgal.h
