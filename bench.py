@@ -11,7 +11,10 @@ One step = one full solve through the C ABI: create the handle from the CSR
 `value` is iterations per second over all ranks (replicas on N GPUs, weak
 scaling).  `e2e` repeats the solve from host buffers with the host<->device
 copies inside the timed region.  The reference arm (`--impl reference`) times
-the FP64 CPU oracle on a bounded sample of the same workload.
+the FP64 CPU oracle on a bounded sample of the same workload.  `serving` runs
+the first 256 requests of the batched-serving workload (Poisson arrivals at
+200 req/s, MaxCut graphs with n log-uniform in [100, 50000]) through the
+server API: solves/s and p50/p99 latency.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
 """
@@ -102,6 +105,69 @@ def aggregate_ranks(local_ms: float, steps: int, T: int, world: int, device=None
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
     return world * steps * T / (total_ms / 1000.0), total_ms
+
+
+SERVE_DESC = ("batched serving slice: Poisson arrivals at 200 req/s, n log-uniform in [100, 50000], average "
+              "degree U[4, 16], unit weights, R=10, solved to relative gap 1e-3 (T_max=3000), FP32 path")
+
+
+def run_serving(S, count: int, slots: int, seed: int, T_max: int = 3000):
+    """The first `count` requests of the batched-serving workload through the
+    server API (submit at the arrival times, poll every result).  Returns the
+    throughput / latency summary and the raw latencies (ms)."""
+    import numpy as np
+    import workloads as W
+    reqs = W.serving_requests(count, rate=200.0, seed=seed)
+    graphs = []
+    for r in reqs:
+        g = W.er_graph(r["n"], r["m"], seed=r["seed"], weights="unit")
+        rp, col, _ = g.csr()
+        graphs.append((rp, col))
+    srv = S.scgal_server_create(64 << 30, slots)
+    t0 = time.perf_counter()
+    tickets = []
+    for r, (rp, col) in zip(reqs, graphs):
+        while time.perf_counter() - t0 < r["arrival_s"]:
+            time.sleep(0.0002)
+        prm = S.scgal_params_default(R=10, T_max=T_max, tol=1e-3, precision=32, seed=r["seed"], instance=r["id"])
+        tickets.append(S.scgal_submit(srv, rp, col, None, r["n"], col.size, prm))
+    res = [S.scgal_poll(srv, t, -1) for t in tickets]
+    wall = time.perf_counter() - t0
+    st = S.scgal_server_get_stats(srv)
+    S.scgal_server_destroy(srv)
+    lat = np.array([x["latency_ms"] for x in res])
+    its = np.array([x["iterations"] for x in res])
+    out = {"requests": count, "slots": slots, "arrival_rate": 200.0, "wall_s": wall, "solves_per_s": count / wall,
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "converged": int(sum(1 for x in res if x["status"] == S.SCGAL_OK)),
+           "failed": int(sum(1 for x in res if x["status"] not in (S.SCGAL_OK, S.SCGAL_ENOTDONE))),
+           "iterations_mean": float(its.mean()), "iter_per_s": float(its.sum()) / wall,
+           "queue_p50_ms": float(np.percentile([x["queue_ms"] for x in res], 50)),
+           "rounds": st["rounds"], "worker_ms": {"wait": st["wait_ms"], "admit": st["admit_ms"],
+                                                  "retire": st["retire_ms"]},
+           "device_bytes_peak": st["device_bytes_peak"], "desc": SERVE_DESC}
+    return out, lat.tolist()
+
+
+def aggregate_serving(local, lat, world: int):
+    """Serving over `world` replicas: requests and iterations summed, the
+    slowest replica's wall time, percentiles over every request."""
+    if world == 1:
+        return local
+    import numpy as np
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, (local, lat))
+    wall = max(p[0]["wall_s"] for p in parts)
+    allat = np.concatenate([np.asarray(p[1]) for p in parts])
+    out = dict(local)
+    out.update({"requests": sum(p[0]["requests"] for p in parts), "wall_s": wall,
+                "solves_per_s": sum(p[0]["requests"] for p in parts) / wall,
+                "iter_per_s": sum(p[0]["iter_per_s"] * p[0]["wall_s"] for p in parts) / wall,
+                "p50_ms": float(np.percentile(allat, 50)), "p99_ms": float(np.percentile(allat, 99)),
+                "converged": sum(p[0]["converged"] for p in parts), "failed": sum(p[0]["failed"] for p in parts),
+                "replicas": world})
+    return out
 
 
 def measured_peaks():
@@ -266,6 +332,11 @@ def main():
     ap.add_argument("--sample-iters", type=int, default=6)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=256,
+                    help="requests of the batched-serving slice (0: skip the serving leg)")
+    ap.add_argument("--serve-slots", type=int, default=152)
+    ap.add_argument("--profile-serve", type=int, default=0,
+                    help="only run K requests of the serving workload with T_max=300 (for profiler captures)")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-reps", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--profile-solve", action="store_true",
@@ -279,6 +350,12 @@ def main():
         return
     if args.profile_solve:
         profile_solve(args.T)
+        return
+    if args.profile_serve:
+        from paper_1912_02949_gb300 import scgal as S
+        S.load()
+        out, _ = run_serving(S, args.profile_serve, args.serve_slots, seed=SEED, T_max=300)
+        print(json.dumps(out))
         return
 
     import numpy as np
@@ -393,6 +470,11 @@ def main():
                 "traffic": profiled_traffic(), "kernel": "k_spmv_step (CSR D-matvec + omega reduction)",
                 "bytes_per_launch": bytes_step, "ms_per_launch": kern["spmv_step"], "peak_source": peak_src}
 
+    serving = None
+    if args.serve_requests > 0:
+        local, lat = run_serving(S, args.serve_requests, args.serve_slots, seed=replica_seed(rank))
+        serving = aggregate_serving(local, lat, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "er2p20":
         cpu = cpu_baseline_entry(run_cpu_sample(args.sample_iters), T)
@@ -411,7 +493,7 @@ def main():
                 "gpu_launches": args.steps * launches_per_solve(n, T),
                 "clocks": clk, "solve": {"relgap_T": last["relgap"], "infeas_T": last["infeas"],
                                          "objective_T": last["p"], "best_cut": cut, "lambda_top3": list(lam[:3])},
-                "kernels_ms_per_launch": kern, "kernel_share_of_solve": share, **extra}
+                "kernels_ms_per_launch": kern, "kernel_share_of_solve": share, "serving": serving, **extra}
         if hist32:
             hit = next((r["t"] for r in hist32 if r["relgap"] <= 1e-3 and r["infeas"] <= 1e-3), None)
             line["solve"]["first_t_gap_1e-3"] = hit
