@@ -203,8 +203,8 @@ int batch_prepare(scgal_ctx* h, void* out);
 // until it converges, reaches T_max, has run `iters` iterations or (after its
 // first iteration) the launch has run for budget_ns; d_status[slot] is written.
 int batch_variant(const void* desc);             // kernel variant of a slot descriptor, < BATCH_NVAR
-constexpr int BATCH_NVAR = 12;
-constexpr int BATCH_CTL_DEADLINE = 16;           // int offset of the deadline in the control block
+constexpr int BATCH_NVAR = 12;                   // 6 one-block variants, 6 clustered
+constexpr int BATCH_CTL_DEADLINE = 24;           // int offset of the deadline in the control block
 constexpr int BATCH_CTL_INTS = 32;               // ints of the control block
 struct BatchLaunch;                              // per-variant streams and events of the launches
 BatchLaunch* batch_launch_create();

@@ -29,8 +29,12 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
 #include "tridiag.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace scgal {
 
@@ -67,7 +71,7 @@ struct BatchSlot {
     const float* cds;      // diagonal of C', slice order
     int nslices;
     int narrow;
-    int variant;           // kernel variant: (narrow, weight kind, D x in shared memory)
+    int variant;           // kernel variant: one block (narrow, weight kind, D x in shared memory) or a cluster
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -132,25 +136,27 @@ __device__ __forceinline__ float add_entry(float acc, int c, float w, const floa
 
 // y = diag .* x + coff * (W x) over the sliced layout, x in shared memory.
 // Writes y_r to yo[r] (unless yo is null) and returns this thread's part of <x, y>.
-// Warp w takes slices w, w + NW, w + 2 NW, ... (similar widths, as slices are
-// sorted by degree).  One load per lane fetches the offsets of 32 of them at a
-// time; SL slices then go together, so the loads of SL x U column pairs (and
-// of the SL row ids and diagonal entries) are all in flight at once.
-template <bool NARROW, int WK>
+// Of tw warps in all (NW in a block; the cluster's warps for a clustered
+// instance), warp gw takes slices gw, gw + tw, gw + 2 tw, ... (similar widths,
+// as slices are sorted by degree).  One load per lane fetches the offsets of 32
+// of them at a time; SL slices then go together, so the loads of SL x U column
+// pairs (and of the SL row ids and diagonal entries) are all in flight at once.
+// L2DG: the diagonal was written by other blocks of the cluster (read from L2).
+template <bool NARROW, int WK, bool L2DG = false>
 __device__ __forceinline__ float bs_matvec(const BatchSlot& B, const float* __restrict__ dg, const float* xs,
-                                           float* yo) {
+                                           float* yo, int gw = threadIdx.x >> 5, int tw = NW) {
     using PT = typename Pair<NARROW>::T;
     constexpr int SL = 4, U = (NARROW && WK != W_REAL) ? 5 : 2;   // pairs in flight within the register budget
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int n = B.p.c.n, ns = B.nslices;
     const float coff = (float)B.p.c.coff;
     const PT* __restrict__ ent = reinterpret_cast<const PT*>(B.ent);
-    const int nmine = (ns - warp + NW - 1) / NW;           // slices of this warp
+    const int nmine = (gw < ns) ? (ns - gw + tw - 1) / tw : 0;   // slices of this warp
     float dot = 0.f;
     for (int j0 = 0; j0 < nmine; j0 += 32) {
         int ol = 0, wl = 0;
         if (j0 + lane < nmine) {
-            const int sl = warp + (j0 + lane) * NW;
+            const int sl = gw + (j0 + lane) * tw;
             ol = B.poff[sl];
             wl = (B.poff[sl + 1] - ol) >> 5;
         }
@@ -169,10 +175,10 @@ __device__ __forceinline__ float bs_matvec(const BatchSlot& B, const float* __re
                 row[k] = n;
                 d[k] = 0.f;
                 if (w2[k] >= 0) {
-                    const int pos = (warp + (j0 + jj + k) * NW) * 32 + lane;
+                    const int pos = (gw + (j0 + jj + k) * tw) * 32 + lane;
                     row[k] = NARROW ? (int)reinterpret_cast<const unsigned short*>(B.rowid)[pos]
                                     : reinterpret_cast<const int*>(B.rowid)[pos];
-                    d[k] = dg[pos];
+                    d[k] = L2DG ? __ldcg(dg + pos) : dg[pos];
                 }
             }
             for (int k0 = 0; k0 < wmax; k0 += U) {
@@ -574,7 +580,8 @@ __device__ __forceinline__ void run_instance(const BatchSlot& B, int iters, unsi
 template <bool NARROW, int WK, bool YS>
 __global__ void __launch_bounds__(BT, 1)
 k_batch(const BatchSlot* __restrict__ slots, const int* __restrict__ active, int nact, int* next,
-        unsigned long long* deadline, int iters, unsigned long long budget_ns, BatchStatus* status) {
+        unsigned long long* deadline, int iters, unsigned long long budget_ns, unsigned long long slice_ns,
+        BatchStatus* status) {
     __shared__ int s_k;
     __shared__ unsigned long long s_deadline;
     __shared__ BatchSlot sb;
@@ -591,7 +598,8 @@ k_batch(const BatchSlot* __restrict__ slots, const int* __restrict__ active, int
         __syncthreads();
         const int k = s_k;
         if (k >= nact) break;
-        run_instance<NARROW, WK, YS>(sb, iters, s_deadline);
+        const unsigned long long own = globaltimer_ns() + slice_ns;   // this instance's share of the round
+        run_instance<NARROW, WK, YS>(sb, iters, own < s_deadline ? own : s_deadline);
         if (threadIdx.x == 0) {
             const DevScalars* sc = sb.p.sc;
             BatchStatus st;
@@ -602,6 +610,500 @@ k_batch(const BatchSlot* __restrict__ slots, const int* __restrict__ active, int
             status[active[k]] = st;
         }
         __syncthreads();                     // sb and s_k are rewritten by the next fetch
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Clustered instances (n >= BATCH_NMIN_CL): a cluster of CL blocks per
+// instance.  Every block keeps all of x in its own shared memory and computes
+// the D-matvec over its share of the slices (warp gw of the cluster's CL * NW
+// warps takes slices gw, gw + CL NW, ...), writing D x to global memory.  Each
+// block owns a contiguous range of rows [lo, hi) for the element-wise steps
+// (Lanczos update, Ritz vector, z / sketch update, dual step) and writes its
+// new entries of x into every block's shared memory (distributed shared
+// memory).  Every cluster barrier is preceded by a memory fence (csync).  Sums: each block's total goes to block 0's shared memory, a
+// cluster barrier, every block adds the CL totals in rank order (so all blocks
+// hold identical totals and take identical decisions), a second barrier.  Global data that
+// another block wrote is read through L2 (__ldcg).  Block 0 alone writes the
+// instance's scalars and runs the tridiagonal solve.
+constexpr int CL = 4;
+constexpr int BATCH_NMIN_CL = 16384;             // smallest n served by a cluster
+constexpr size_t BATCH_SMEM_CL = sizeof(float) * (size_t)LOFF + TSM_BYTES;   // x, then the tridiagonal scratch
+static_assert(BATCH_NMIN_CL <= BATCH_NMAX_Y + 1, "one-block instances keep D x in shared memory");
+
+__shared__ double b_cred[2][CL * RED_NV];       // per-block totals, in block 0 (two alternating sets)
+
+// Cluster barrier with every earlier write of this thread made visible first.
+// (The barrier alone did not order the blocks' writes here: without the fence,
+// four-block clusters gave run-to-run different results on GB300.)
+__device__ __forceinline__ void csync() {
+    __threadfence();
+    cg::this_cluster().sync();
+}
+
+struct ClCtx {
+    unsigned rank;
+    int lo, hi;    // this block's rows
+    int par;       // set of b_cred the next sum uses
+};
+
+// Cluster-wide totals of NV per-block totals (identical in every thread of every block).
+template <int NV>
+__device__ __forceinline__ void csum(const double (&blk)[NV], double (&out)[NV], ClCtx& cx) {
+    cg::cluster_group cl = cg::this_cluster();
+    double* buf = &b_cred[cx.par][0];
+    if (threadIdx.x == 0) {
+        double* dst = cl.map_shared_rank(buf, 0);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) dst[cx.rank * NV + k] = blk[k];
+    }
+    csync();                                     // also publishes every block's earlier writes
+    double* res = b_red + NW * RED_NV;
+    if (threadIdx.x < NV) {
+        const double* src = cl.map_shared_rank(buf, 0);
+        double t = 0.0;
+        for (int c = 0; c < CL; ++c) t += src[c * NV + threadIdx.x];
+        res[threadIdx.x] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = res[k];
+    csync();                                     // every block has read the totals
+    cx.par ^= 1;
+}
+
+// Lanczos (as b_lanczos).  Returns 0, 1 on breakdown (rho == 0), 2 on a non-finite value.
+template <bool NARROW, int WK>
+__device__ __forceinline__ int c_lanczos(const BatchSlot& B, int q, ClCtx& cx) {
+    constexpr int U = 8;
+    cg::cluster_group cl = cg::this_cluster();
+    const KP<float>& p = B.p;
+    DevScalars* sc = p.sc;
+    const int n = p.c.n;
+    const size_t ldb = (size_t)p.ldb;
+    float* xs = b_smem;
+    float* peer[CL];
+#pragma unroll
+    for (int c = 0; c < CL; ++c) peer[c] = cl.map_shared_rank(xs, c);
+    const bool lead = cx.rank == 0 && threadIdx.x == 0;
+    for (int r = threadIdx.x; r < n; r += BT) xs[r] = __ldcg(p.basis + r);   // W_0, written by all blocks
+    __syncthreads();
+    double si = __ldcg(p.sv), s_prev = 0.0, rho_prev = 0.0;
+    for (int i = 0; i < q; ++i) {
+        const float d[1] = {bs_matvec<NARROW, WK, true>(B, B.dvs, xs, p.ybuf, (int)cx.rank * NW + (threadIdx.x >> 5),
+                                                         CL * NW)};
+        double Db[1], D[1];
+        bsum<1>(d, Db);
+        csum<1>(Db, D, cx);                      // D x of every block now visible in global memory
+        const double om = si * si * D[0];
+        if (lead) {
+            if (!isfinite(om)) {
+                sc->err = SCGAL_ENUMERIC;
+                sc->converged = 1;
+            }
+            p.om[i] = om;
+            sc->k = i + 1;
+        }
+        if (!isfinite(om)) return 2;
+        if (i == q - 1) break;
+        const float a = (float)si, b = (float)(-om * si), c = (float)(i > 0 ? -rho_prev * s_prev : 0.0);
+        const float* __restrict__ Wm = p.basis + (size_t)(i > 0 ? i - 1 : i) * ldb;
+        float* __restrict__ Wn = p.basis + (size_t)(i + 1) * ldb;
+        float acc[1] = {0.f};
+        for (int base = cx.lo + threadIdx.x; base < cx.hi; base += BT * U) {
+            float wm[U], yy[U], xx[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int r = base + u * BT;
+                const bool in = r < cx.hi;
+                wm[u] = in ? Wm[r] : 0.f;        // this block's rows of W_{i-1}: written by this block
+                yy[u] = in ? __ldcg(p.ybuf + r) : 0.f;
+                xx[u] = in ? xs[r] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int r = base + u * BT;
+                if (r < cx.hi) {
+                    const float w = fmaf(a, yy[u], fmaf(b, xx[u], c * wm[u]));
+                    Wn[r] = w;
+#pragma unroll
+                    for (int cc = 0; cc < CL; ++cc) peer[cc][r] = w;   // every block's copy of x
+                    acc[0] += w * w;
+                }
+            }
+        }
+        double Rb[1], RR[1];
+        bsum<1>(acc, Rb);
+        csum<1>(Rb, RR, cx);                     // every block's x complete after this barrier
+        const double rho = sqrt(RR[0]);
+        if (rho == 0.0 || !isfinite(rho)) {
+            if (lead) {
+                sc->stop = 1;
+                if (rho != 0.0) {
+                    sc->err = SCGAL_ENUMERIC;
+                    sc->converged = 1;
+                }
+            }
+            return rho == 0.0 ? 1 : 2;
+        }
+        if (lead) {
+            p.rh[i] = rho;
+            p.sv[i + 1] = 1.0 / rho;
+        }
+        s_prev = si;
+        si = 1.0 / rho;
+        rho_prev = rho;
+    }
+    return 0;
+}
+
+// Ritz vector of this block's rows into every block's x, ||v||^2 and v* Omega.
+// Returns false on a non-finite or zero norm.  tot: the cluster totals.
+template <int RT>
+__device__ __forceinline__ bool c_ritz(const BatchSlot& B, ClCtx& cx, double (&tot)[1 + BATCH_RMAX]) {
+    constexpr int NV = 1 + RT;
+    constexpr int U = 4;
+    cg::cluster_group cl = cg::this_cluster();
+    const KP<float>& p = B.p;
+    DevScalars* sc = p.sc;
+    const int k = __ldcg(&sc->k), R = p.c.R;
+    const size_t ldb = (size_t)p.ldb;
+    float* cf = b_smem + LOFF;
+    float* peer[CL];
+#pragma unroll
+    for (int c = 0; c < CL; ++c) peer[c] = cl.map_shared_rank(b_smem, c);
+    for (int j = threadIdx.x; j < k; j += BT) cf[j] = (float)__ldcg(p.coef + j);
+    __syncthreads();
+    float acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.f;
+    for (int base = cx.lo + threadIdx.x; base < cx.hi; base += BT * U) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = 0.f;
+        int j = 0;
+        for (; j + 4 <= k; j += 4) {
+            float w[4][U];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int r = base + u * BT;
+                    w[jj][u] = (r < cx.hi) ? p.basis[(size_t)(j + jj) * ldb + r] : 0.f;
+                }
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                for (int u = 0; u < U; ++u) v[u] = fmaf(cf[j + jj], w[jj][u], v[u]);
+        }
+        for (; j < k; ++j)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int r = base + u * BT;
+                if (r < cx.hi) v[u] = fmaf(cf[j], p.basis[(size_t)j * ldb + r], v[u]);
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int r = base + u * BT;
+            if (r < cx.hi) {
+#pragma unroll
+                for (int cc = 0; cc < CL; ++cc) peer[cc][r] = v[u];
+                acc[0] += v[u] * v[u];
+                const float* om = p.Omega + (size_t)r * R;
+#pragma unroll
+                for (int c = 0; c < RT; ++c)
+                    if (c < R) acc[1 + c] += v[u] * om[c];
+            }
+        }
+    }
+    double blk[NV], t[NV];
+    bsum<NV>(acc, blk);
+    csum<NV>(blk, t, cx);                        // every block's x holds all of v after this barrier
+#pragma unroll
+    for (int i = 0; i < NV; ++i) tot[i] = t[i];
+    if (cx.rank == 0 && threadIdx.x == 0) {
+        sc->nv2 = t[0];
+        for (int c = 0; c < R; ++c) {
+            sc->r[2 * c] = t[1 + c];
+            sc->r[2 * c + 1] = 0.0;
+        }
+        if (!(t[0] > 0.0) || !isfinite(t[0])) {
+            sc->err = SCGAL_ENUMERIC;
+            sc->converged = 1;
+        }
+    }
+    return t[0] > 0.0 && isfinite(t[0]);
+}
+
+// v* C v, z and sketch updates of this block's rows, objective / trace, and
+// the dual step size (identical in every block; block 0 records it).
+template <bool NARROW, int WK>
+__device__ __forceinline__ double c_vcv_update(const BatchSlot& B, ClCtx& cx, const double (&tot)[1 + BATCH_RMAX],
+                                               long long t) {
+    constexpr int U = 4;
+    const KP<float>& p = B.p;
+    DevScalars* sc = p.sc;
+    const int R = p.c.R;
+    const float* xs = b_smem;
+    float* rs = b_rs;
+    const float vcv = bs_matvec<NARROW, WK, true>(B, B.cds, xs, nullptr, (int)cx.rank * NW + (threadIdx.x >> 5),
+                                                  CL * NW);
+    const double eta = __ldcg(&sc->eta), nv2 = tot[0];
+    const int take = __ldcg(&sc->take_h);
+    const double zc = take ? eta * p.c.alpha * p.c.sA / nv2 : 0.0;
+    const float sfac = take ? (float)(eta * p.c.alpha / nv2) : 0.f;
+    const float om1 = (float)(1.0 - eta);
+    if (threadIdx.x < R) rs[threadIdx.x] = (float)tot[1 + threadIdx.x];
+    double a_nzb = 0.0, a_yzb = 0.0, a_yy = 0.0;
+    for (int base = cx.lo + threadIdx.x; base < cx.hi; base += BT * U) {
+        double zo[U], bb[U], yo[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = base + u * BT;
+            zo[u] = (e < cx.hi) ? p.z[e] : 0.0;
+            bb[u] = (e < cx.hi && !p.c.b_const) ? p.b[e] : p.c.bconst;
+            yo[u] = (e < cx.hi && p.c.K_finite) ? p.y[e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = base + u * BT;
+            if (e < cx.hi) {
+                const double ve = (double)xs[e];
+                const double zi = fma(1.0 - eta, zo[u], zc * ve * ve);
+                p.z[e] = zi;
+                const double zb = zi - bb[u];
+                a_nzb = fma(zb, zb, a_nzb);
+                if (p.c.K_finite) {
+                    a_yzb = fma(yo[u], zb, a_yzb);
+                    a_yy = fma(yo[u], yo[u], a_yy);
+                }
+            }
+        }
+    }
+    __syncthreads();                             // rs
+    // this block's rows of S (row-major n x R); lo is a multiple of 4, so the
+    // groups of four entries start at lo * R
+    const int k_lo = cx.lo * R, k_hi = cx.hi * R;
+    const int g_lo = k_lo >> 2, g_hi = k_hi >> 2;
+    float4* S4 = reinterpret_cast<float4*>(p.S);
+    for (int g0 = g_lo + threadIdx.x; g0 < g_hi; g0 += BT * U) {
+        float4 sv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (g0 + u * BT < g_hi) sv[u] = S4[g0 + u * BT];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int g = g0 + u * BT;
+            if (g < g_hi) {
+                int e = (4 * g) / R, c = 4 * g - e * R;
+                float* f = &sv[u].x;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    f[m] = fmaf(om1, f[m], sfac * xs[e] * rs[c]);
+                    if (++c == R) {
+                        c = 0;
+                        ++e;
+                    }
+                }
+                S4[g] = sv[u];
+            }
+        }
+    }
+    for (int kk = 4 * g_hi + threadIdx.x; kk < k_hi; kk += BT) {
+        const int e = kk / R, c = kk - e * R;
+        p.S[kk] = fmaf(om1, p.S[kk], sfac * xs[e] * rs[c]);
+    }
+    double bb4[4];
+    {
+        const float f[1] = {vcv};
+        double F[1];
+        bsum<1>(f, F);
+        double rest[3];
+        const double dd[3] = {a_nzb, a_yzb, a_yy};
+        bsum<3>(dd, rest);
+        const double all[4] = {F[0], rest[0], rest[1], rest[2]};
+        csum<4>(all, bb4, cx);
+    }
+    const Consts& c = p.c;
+    const double nzb2 = bb4[1];
+    double gamma = (nzb2 == 0.0) ? c.beta0
+                                 : fmin(c.beta0, 4.0 * c.alpha * c.alpha * c.beta0 * c.normA_s * c.normA_s /
+                                                     (pow((double)(t + 1), 1.5) * nzb2));
+    if (c.K_finite) {
+        const double yy = bb4[3] + 2.0 * gamma * bb4[2] + gamma * gamma * nzb2;
+        if (sqrt(yy) > c.K) gamma = 0.0;
+    }
+    if (cx.rank == 0 && threadIdx.x == 0) {
+        const double vcvn = bb4[0] / nv2;
+        sc->vCv = vcvn;
+        sc->p = (1.0 - eta) * sc->p + (take ? eta * c.alpha * vcvn : 0.0);
+        sc->tau = (1.0 - eta) * sc->tau + (take ? eta * c.alpha : 0.0);
+        sc->gamma = gamma;
+        sc->nzb2_new = nzb2;
+        p.hist[(t - 1) % c.hist_cap].gamma = gamma;
+    }
+    return gamma;
+}
+
+// Dual step and set-up of iteration t + 1 on this block's rows (as b_dual_start).
+template <bool NARROW>
+__device__ __forceinline__ void c_dual_start(const BatchSlot& B, ClCtx& cx, double gamma, long long t) {
+    constexpr int U = 4;
+    const KP<float>& p = B.p;
+    DevScalars* sc = p.sc;
+    const long long t1 = t + 1;
+    const double beta1 = p.c.beta0 * sqrt((double)(t1 + 1));
+    double a[3] = {0.0, 0.0, 0.0};
+    float w0 = 0.f;
+    for (int base = cx.lo + threadIdx.x; base < cx.hi; base += BT * U) {
+        double bb[U], zz[U], yy[U];
+        float cd[U];
+        int pv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = base + u * BT;
+            const bool in = i < cx.hi;
+            bb[u] = (in && !p.c.b_const) ? p.b[i] : p.c.bconst;
+            zz[u] = in ? p.z[i] : 0.0;
+            yy[u] = in ? p.y[i] : 0.0;
+            cd[u] = in ? p.cdiag[i] : 0.f;
+            pv[u] = in ? (NARROW ? (int)reinterpret_cast<const unsigned short*>(B.pinv)[i]
+                                 : reinterpret_cast<const int*>(B.pinv)[i])
+                       : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = base + u * BT;
+            if (i < cx.hi) {
+                const double bi = bb[u], zi = zz[u];
+                const double zb = zi - bi;
+                const double yi = fma(gamma, zb, yy[u]);
+                p.y[i] = yi;
+                a[0] = fma(yi, bi, a[0]);
+                a[1] = fma(zb, zi + bi, a[1]);
+                a[2] = fma(zb, zb, a[2]);
+                const double wi = p.c.sA * fma(beta1, zb, yi);
+                B.dvs[pv[u]] = (float)((double)cd[u] + wi);
+            }
+        }
+    }
+    // start vector of iteration t + 1: the normal pairs (2 pr, 2 pr + 1) of this block's rows
+    const unsigned tt = (unsigned)t1;
+    for (int pr = (cx.lo >> 1) + threadIdx.x; 2 * pr < cx.hi; pr += BT) {
+        float n0, n1;
+        normal_pair(p.c.seed, PURPOSE_LANCZOS, tt, p.c.instance, (unsigned)pr, n0, n1);
+        p.basis[2 * pr] = n0;
+        w0 += n0 * n0;
+        if (2 * pr + 1 < cx.hi) {
+            p.basis[2 * pr + 1] = n1;
+            w0 += n1 * n1;
+        }
+    }
+    double blk[4];
+    {
+        double A[3], W[1];
+        bsum<3>(a, A);
+        const float wf[1] = {w0};
+        bsum<1>(wf, W);
+        const double all[4] = {A[0], A[1], A[2], W[0]};
+        csum<4>(all, blk, cx);                   // the new dvec and W_0 visible after this barrier
+    }
+    if (cx.rank == 0 && threadIdx.x == 0) {
+        sc->t = t1;
+        sc->beta = beta1;
+        sc->eta = 2.0 / (double)(t1 + 1);
+        sc->yb = blk[0];
+        sc->zbzpb = blk[1];
+        sc->nzb2 = blk[2];
+        p.sv[0] = 1.0 / sqrt(blk[3]);
+        sc->k = 0;
+        sc->stop = 0;
+        sc->take_h = 1;
+    }
+}
+
+// Iterations of one clustered instance (as run_instance); every block of the
+// cluster runs this with the same arguments.
+template <bool NARROW, int WK>
+__device__ __forceinline__ void run_instance_cl(const BatchSlot& B, int iters, unsigned long long deadline) {
+    cg::cluster_group cl = cg::this_cluster();
+    const KP<float>& p = B.p;
+    DevScalars* sc = p.sc;
+    const int n = p.c.n;
+    ClCtx cx;
+    cx.rank = cl.block_rank();
+    const int chunk = ((n + CL - 1) / CL + 3) & ~3;   // multiple of 4: whole sketch float4 groups, even start
+    cx.lo = min(n, (int)cx.rank * chunk);
+    cx.hi = min(n, cx.lo + chunk);
+    cx.par = 0;
+    double* tsm = reinterpret_cast<double*>(b_smem + LOFF);
+    if (threadIdx.x == 0) b_smem[n] = 0.f;       // padding rows and entries read x_n
+    const int* go0 = cl.map_shared_rank(&b_go, 0);
+    for (int it = 0; it < iters; ++it) {
+        if (cx.rank == 0 && threadIdx.x == 0)
+            b_go = !sc->converged && sc->t <= p.c.hist_cap && (it == 0 || globaltimer_ns() < deadline);
+        csync();
+        if (!*go0) break;                        // block 0's decision, read by every block
+        const long long t = __ldcg(&sc->t);
+        const int q = p.qtab[t - 1];
+        const int lz = c_lanczos<NARROW, WK>(B, q, cx);
+        if (lz == 2) break;
+        if (cx.rank == 0) tridiag_body<float>(p, q, tsm);
+        csync();                                 // coefficients, xi, stopping decision
+        if (__ldcg(&sc->converged)) break;
+        double tot[1 + BATCH_RMAX];
+        bool ok;
+        if (p.c.R <= 4) ok = c_ritz<4>(B, cx, tot);
+        else if (p.c.R <= 8) ok = c_ritz<8>(B, cx, tot);
+        else ok = c_ritz<16>(B, cx, tot);
+        if (!ok) break;
+        const double gamma = c_vcv_update<NARROW, WK>(B, cx, tot, t);
+        c_dual_start<NARROW>(B, cx, gamma, t);
+    }
+    csync();          // every block done with every other block's shared memory
+}
+
+// One persistent launch per clustered kernel variant (as k_batch, with
+// clusters of CL blocks taking the instances).
+template <bool NARROW, int WK>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(BT, 1)
+k_batch_cl(const BatchSlot* __restrict__ slots, const int* __restrict__ active, int nact, int* next,
+           unsigned long long* deadline, int iters, unsigned long long budget_ns, unsigned long long slice_ns,
+           BatchStatus* status) {
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ int s_k;
+    __shared__ unsigned long long s_deadline, s_idl;
+    __shared__ BatchSlot sb;
+    const bool lead = cl.block_rank() == 0 && threadIdx.x == 0;
+    if (lead) {
+        const unsigned long long mine = globaltimer_ns() + budget_ns;
+        const unsigned long long old = atomicCAS(deadline, 0ull, mine);
+        s_deadline = old ? old : mine;
+    }
+    const int* k0 = cl.map_shared_rank(&s_k, 0);
+    const unsigned long long* dl0 = cl.map_shared_rank(&s_idl, 0);
+    for (;;) {
+        if (lead) {
+            s_k = atomicAdd(next, 1);
+            const unsigned long long own = globaltimer_ns() + slice_ns;   // this instance's share of the round
+            s_idl = own < s_deadline ? own : s_deadline;
+        }
+        csync();
+        const int k = *k0;                       // block 0's fetch, read by every block
+        const unsigned long long dl = *dl0;
+        if (k < nact && threadIdx.x == 0) sb = slots[active[k]];
+        csync();                                 // s_k read everywhere before block 0 rewrites it
+        if (k >= nact) break;
+        run_instance_cl<NARROW, WK>(sb, iters, dl);
+        if (lead) {
+            const DevScalars* sc = sb.p.sc;
+            BatchStatus st;
+            st.t = sc->t;
+            st.conv_t = sc->conv_t;
+            st.converged = sc->converged;
+            st.err = sc->err;
+            status[active[k]] = st;
+        }
     }
 }
 
@@ -706,7 +1208,7 @@ int batch_prepare(scgal_ctx* h, void* out) {
     b.p = p;
     b.nslices = nslices;
     b.narrow = narrow;
-    b.variant = (narrow ? 6 : 0) + 2 * h->c.wkind + (n <= BATCH_NMAX_Y ? 1 : 0);
+    b.variant = (n >= BATCH_NMIN_CL ? 6 : 0) + (narrow ? 3 : 0) + h->c.wkind;
     void *ent = nullptr, *sval = nullptr, *poff_d = nullptr, *rowid = nullptr, *pinv = nullptr, *dvs = nullptr,
          *cds = nullptr;
     int rc = ctx_alloc(h, &ent, (size_t)std::max<long long>(npairs, 1) * (narrow ? 4 : 8));
@@ -751,16 +1253,19 @@ struct BatchLaunch {
 };
 
 using BatchKernel = void (*)(const BatchSlot*, const int*, int, int*, unsigned long long*, int, unsigned long long,
-                             BatchStatus*);
+                             unsigned long long, BatchStatus*);
 
 static BatchKernel variant_kernel(int v) {
+    // one block per instance: n < BATCH_NMIN_CL <= BATCH_NMAX_Y, so x and D x are in shared memory
     static const BatchKernel tab[BATCH_NVAR] = {
-        k_batch<false, W_UNIT, false>, k_batch<false, W_UNIT, true>, k_batch<false, W_PM1, false>,
-        k_batch<false, W_PM1, true>,   k_batch<false, W_REAL, false>, k_batch<false, W_REAL, true>,
-        k_batch<true, W_UNIT, false>,  k_batch<true, W_UNIT, true>,  k_batch<true, W_PM1, false>,
-        k_batch<true, W_PM1, true>,    k_batch<true, W_REAL, false>, k_batch<true, W_REAL, true>};
+        k_batch<false, W_UNIT, true>, k_batch<false, W_PM1, true>, k_batch<false, W_REAL, true>,
+        k_batch<true, W_UNIT, true>,  k_batch<true, W_PM1, true>,  k_batch<true, W_REAL, true>,
+        k_batch_cl<false, W_UNIT>,    k_batch_cl<false, W_PM1>,    k_batch_cl<false, W_REAL>,
+        k_batch_cl<true, W_UNIT>,     k_batch_cl<true, W_PM1>,     k_batch_cl<true, W_REAL>};
     return tab[v];
 }
+
+static bool clustered(int v) { return v >= 6; }
 
 BatchLaunch* batch_launch_create() {
     BatchLaunch* L = new BatchLaunch();
@@ -794,34 +1299,67 @@ int batch_variant(const void* desc) { return reinterpret_cast<const BatchSlot*>(
 int launch_batch(BatchLaunch* L, const void* d_slots, const int* d_active, const int* counts, int* d_ctl, int iters,
                  unsigned long long budget_ns, BatchStatus* d_status, cudaStream_t s) {
     static int ready = 0;
-    static int sms = 1;
+    static int sms = 1, max_clusters = 1;
     if (!ready) {
         for (int v = 0; v < BATCH_NVAR; ++v)
             if (cudaFuncSetAttribute(variant_kernel(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)BATCH_SMEM) != cudaSuccess)
+                                     (int)(clustered(v) ? BATCH_SMEM_CL : BATCH_SMEM)) != cudaSuccess)
                 return SCGAL_ECUDA;
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(CL, 1, 1);
+        cfg.blockDim = dim3(BT, 1, 1);
+        cfg.dynamicSmemBytes = BATCH_SMEM_CL;
+        int mc = 0;
+        if (cudaOccupancyMaxActiveClusters(&mc, (const void*)variant_kernel(9), &cfg) != cudaSuccess || mc < 1) {
+            cudaGetLastError();
+            mc = sms / (2 * CL);
+        }
+        max_clusters = std::max(1, std::min(mc, sms / CL));
         ready = 1;
     }
+    // Blocks: clustered instances first (CL SMs each), in proportion to the
+    // SMs the two kinds of instance would occupy; every launched variant gets
+    // at least one block (cluster).  Within a variant, instances beyond its
+    // blocks share them in time slices of the round.
+    long long ncl = 0, nsg = 0;
+    for (int v = 0; v < BATCH_NVAR; ++v) (clustered(v) ? ncl : nsg) += std::max(0, counts[v]);
+    int cl_budget = 0;
+    if (ncl > 0) {
+        const double want = (double)ncl * CL;
+        const double share = nsg > 0 ? sms * want / (want + (double)nsg) : (double)sms;
+        cl_budget = std::max(1, std::min<int>(max_clusters, (int)std::min<double>((double)ncl, share / CL)));
+    }
+    const int sg_budget = std::max(1, sms - CL * cl_budget);
     // d_ctl: BATCH_NVAR work counters, then the round's deadline (8-byte aligned)
     unsigned long long* deadline = reinterpret_cast<unsigned long long*>(d_ctl + BATCH_CTL_DEADLINE);
     if (cudaMemsetAsync(d_ctl, 0, sizeof(int) * BATCH_CTL_INTS, s) != cudaSuccess ||
         cudaEventRecord(L->start, s) != cudaSuccess)
         return SCGAL_ECUDA;
-    int off = 0;
-    for (int v = 0; v < BATCH_NVAR; ++v) {
-        const int c = counts[v];
-        if (c <= 0) continue;
-        if (cudaStreamWaitEvent(L->s[v], L->start, 0) != cudaSuccess) return SCGAL_ECUDA;
-        variant_kernel(v)<<<std::min(sms, c), BT, BATCH_SMEM, L->s[v]>>>(
-            reinterpret_cast<const BatchSlot*>(d_slots), d_active + off, c, d_ctl + v, deadline, iters, budget_ns,
-            d_status);
-        if (cudaGetLastError() != cudaSuccess || cudaEventRecord(L->done[v], L->s[v]) != cudaSuccess ||
-            cudaStreamWaitEvent(s, L->done[v], 0) != cudaSuccess)
-            return SCGAL_ECUDA;
-        off += c;
+    int off[BATCH_NVAR];
+    for (int v = 0, o = 0; v < BATCH_NVAR; ++v) {
+        off[v] = o;
+        o += std::max(0, counts[v]);
+    }
+    for (int pass = 0; pass < 2; ++pass) {        // clustered variants are launched first
+        for (int v = 0; v < BATCH_NVAR; ++v) {
+            const int c = counts[v];
+            if (c <= 0 || clustered(v) != (pass == 0)) continue;
+            const long long group = clustered(v) ? ncl : nsg;
+            const int budget_units = clustered(v) ? cl_budget : sg_budget;
+            const int units = (int)std::max<long long>(1, std::min<long long>(c, (long long)budget_units * c / group));
+            const unsigned long long slice = units >= c ? budget_ns : budget_ns * (unsigned long long)units / c;
+            if (cudaStreamWaitEvent(L->s[v], L->start, 0) != cudaSuccess) return SCGAL_ECUDA;
+            const int grid = clustered(v) ? units * CL : units;
+            variant_kernel(v)<<<grid, BT, clustered(v) ? BATCH_SMEM_CL : BATCH_SMEM, L->s[v]>>>(
+                reinterpret_cast<const BatchSlot*>(d_slots), d_active + off[v], c, d_ctl + v, deadline, iters,
+                budget_ns, slice, d_status);
+            if (cudaGetLastError() != cudaSuccess || cudaEventRecord(L->done[v], L->s[v]) != cudaSuccess ||
+                cudaStreamWaitEvent(s, L->done[v], 0) != cudaSuccess)
+                return SCGAL_ECUDA;
+        }
     }
     return SCGAL_OK;
 }

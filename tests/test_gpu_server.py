@@ -103,3 +103,57 @@ def test_poll_timeout_and_unknown_ticket(S):
     assert S.scgal_poll(srv, t, 0) is None            # not finished yet
     assert S.scgal_poll(srv, t, -1) is not None
     S.scgal_server_destroy(srv)
+
+
+def test_alone_equals_mixed_with_clustered_instances(S):
+    """Instances with n >= 16384 run on a cluster of four blocks (x copied into
+    every block's shared memory, sums combined across the cluster in a fixed
+    order); their results, and those of small instances sharing the rounds, are
+    identical alone and mixed."""
+    sizes = [(20000, 8), (300, 6), (40000, 6), (1500, 10), (17000, 12), (800, 8)]
+    reqs = []
+    for k, (n, deg) in enumerate(sizes):
+        g = W.er_graph(n, n * deg // 2, seed=100 + k, weights="unit" if k % 3 else "pm1")
+        rp, col, val = g.csr()
+        reqs.append((k, g, rp, col, val if g.weight_kind != "unit" else None))
+
+    def prm(k):
+        return S.scgal_params_default(R=10, T_max=60, tol=0.0, precision=32, seed=7, instance=k)
+
+    srv = S.scgal_server_create(1 << 34, 8)
+    tickets = [S.scgal_submit(srv, rp, col, val, g.n, col.size, prm(k)) for k, g, rp, col, val in reqs]
+    mixed = [S.scgal_poll(srv, t, -1) for t in tickets]
+    for (k, g, rp, col, val), res in zip(reqs, mixed):
+        alone = S.scgal_poll(srv, S.scgal_submit(srv, rp, col, val, g.n, col.size, prm(k)), -1)
+        assert res["status"] == S.SCGAL_ENOTDONE and res["iterations"] == 60
+        assert _result_fields(res) == _result_fields(alone)
+    S.scgal_server_destroy(srv)
+
+
+def test_clustered_solve_matches_oracle():
+    """A clustered instance (n = 20000, unit weights) served against the FP64
+    oracle on the same random draws.  After one update (the record of t = 2) the
+    trajectories still coincide: objective and infeasibility to 1e-5 relative.
+    At T = 150 every FP32 path, the per-handle graph path included, sits about
+    0.5% from the FP64 trajectory on this graph (measured: graph path -64786,
+    clustered -64677, oracle -65101; the oracle's own spread under 1e-7
+    perturbations of its start vectors is 1e-4), so the bar there is 1.5%
+    on the objective and 5% on the infeasibility."""
+    from paper_1912_02949_gb300 import scgal as S
+    from oracle.problems import MaxCutProblem
+    from oracle.sketchycgal import sketchy_cgal
+    S.load()
+    g = W.er_graph(20000, 80000, seed=5, weights="unit")
+    rp, col, _ = g.csr()
+    srv = S.scgal_server_create(1 << 33, 2)
+    res = {}
+    for T in (2, 150):
+        res[T] = S.scgal_poll(srv, S.scgal_submit(srv, rp, col, None, g.n, col.size,
+                                                  S.scgal_params_default(R=10, T_max=T, tol=0.0, precision=32)), -1)
+    S.scgal_server_destroy(srv)
+    hist = sketchy_cgal(MaxCutProblem(g.n, g.i, g.j, g.w), R=10, T=150, seed=0).history
+    for T, rtol_p, rtol_i in ((2, 1e-5, 1e-5), (150, 1.5e-2, 5e-2)):
+        ref = hist[T - 1]
+        assert res[T]["status"] == S.SCGAL_ENOTDONE and res[T]["iterations"] == T
+        assert abs(res[T]["objective"] - ref["p_orig"]) <= rtol_p * abs(ref["p_orig"])
+        assert abs(res[T]["infeas"] - ref["infeas"]) <= rtol_i * ref["infeas"]
