@@ -10,6 +10,8 @@
 #include <cstring>
 #include <vector>
 
+#include <mutex>
+
 #include "internal.h"
 
 using namespace scgal;
@@ -897,13 +899,40 @@ int do_history(scgal_ctx* h, long long first, long long count, scgal_stats* out)
     return SCGAL_OK;
 }
 
+// Pinned 16-byte slots for the handles' convergence flags, carved from slabs
+// that live as long as the process: cudaHostAlloc / cudaFreeHost per handle
+// would synchronise the device under the other handles' running work.
+std::mutex g_pin_mu;
+std::vector<int*> g_pin_free;
+
+int* pinned_flag_alloc() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        constexpr int kSlots = 4096;
+        int* slab = nullptr;
+        if (cudaHostAlloc((void**)&slab, sizeof(int) * 4 * kSlots, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (int i = kSlots - 1; i >= 0; --i) g_pin_free.push_back(slab + 4 * i);
+    }
+    int* p = g_pin_free.back();
+    g_pin_free.pop_back();
+    return p;
+}
+
+void pinned_flag_free(int* p) {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
 void free_ctx(scgal_ctx* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    if (h->flag_host) cudaFreeHost(h->flag_host);
+    if (h->flag_host) pinned_flag_free(h->flag_host);
     if (h->flag_event) cudaEventDestroy(h->flag_event);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -923,7 +952,8 @@ int common_open(scgal_ctx* h) {
     CUDA_TRY(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     h->own_stream = true;
     CUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-    CUDA_TRY(h, cudaHostAlloc((void**)&h->flag_host, sizeof(int) * 4, cudaHostAllocDefault));
+    h->flag_host = pinned_flag_alloc();
+    if (!h->flag_host) return set_err(h, SCGAL_ENOMEM, "pinned host allocation failed");
     CUDA_TRY(h, cudaEventCreateWithFlags(&h->flag_event, cudaEventDisableTiming));
     return SCGAL_OK;
 }

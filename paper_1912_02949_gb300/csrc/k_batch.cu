@@ -627,6 +627,7 @@ k_batch(const BatchSlot* __restrict__ slots, const int* __restrict__ active, int
 // another block wrote is read through L2 (__ldcg).  Block 0 alone writes the
 // instance's scalars and runs the tridiagonal solve.
 constexpr int CL = 4;
+constexpr int BATCH_RESERVE_SMS = 8;             // left free by the batched launches
 constexpr int BATCH_NMIN_CL = 16384;             // smallest n served by a cluster
 constexpr size_t BATCH_SMEM_CL = sizeof(float) * (size_t)LOFF + TSM_BYTES;   // x, then the tridiagonal scratch
 static_assert(BATCH_NMIN_CL <= BATCH_NMAX_Y + 1, "one-block instances keep D x in shared memory");
@@ -1323,16 +1324,18 @@ int launch_batch(BatchLaunch* L, const void* d_slots, const int* d_active, const
     // Blocks: clustered instances first (CL SMs each), in proportion to the
     // SMs the two kinds of instance would occupy; every launched variant gets
     // at least one block (cluster).  Within a variant, instances beyond its
-    // blocks share them in time slices of the round.
+    // blocks share them in time slices of the round.  BATCH_RESERVE_SMS stay
+    // free for the kernels that set up and retire solves while a round runs.
+    const int avail = std::max(CL + 1, sms - BATCH_RESERVE_SMS);
     long long ncl = 0, nsg = 0;
     for (int v = 0; v < BATCH_NVAR; ++v) (clustered(v) ? ncl : nsg) += std::max(0, counts[v]);
     int cl_budget = 0;
     if (ncl > 0) {
         const double want = (double)ncl * CL;
-        const double share = nsg > 0 ? sms * want / (want + (double)nsg) : (double)sms;
+        const double share = nsg > 0 ? avail * want / (want + (double)nsg) : (double)avail;
         cl_budget = std::max(1, std::min<int>(max_clusters, (int)std::min<double>((double)ncl, share / CL)));
     }
-    const int sg_budget = std::max(1, sms - CL * cl_budget);
+    const int sg_budget = std::max(1, avail - CL * cl_budget);
     // d_ctl: BATCH_NVAR work counters, then the round's deadline (8-byte aligned)
     unsigned long long* deadline = reinterpret_cast<unsigned long long*>(d_ctl + BATCH_CTL_DEADLINE);
     if (cudaMemsetAsync(d_ctl, 0, sizeof(int) * BATCH_CTL_INTS, s) != cudaSuccess ||
