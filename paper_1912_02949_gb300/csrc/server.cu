@@ -94,7 +94,7 @@ struct scgal_server {
     long long rounds_done = 0;
     int active = 0;
     static constexpr int CHUNK = 8;          // iterations per graph-path slot per round
-    static constexpr unsigned long long BATCH_BUDGET_NS = 10000000ull;   // batched launch time per round
+    static constexpr unsigned long long BATCH_BUDGET_NS = 25000000ull;   // batched launch time per round
     static constexpr size_t QUEUE_MAX = 1 << 16;
     // batched engine state (device arrays owned by the worker thread)
     cudaStream_t bstream = nullptr;
