@@ -12,7 +12,7 @@
 
 #include <mutex>
 
-#include "internal.h"
+#include "batch.h"
 
 using namespace scgal;
 

@@ -31,7 +31,7 @@
 
 #include <cooperative_groups.h>
 
-#include "internal.h"
+#include "batch.h"
 #include "tridiag.cuh"
 
 namespace cg = cooperative_groups;

@@ -25,7 +25,7 @@
 #include <thread>
 #include <vector>
 
-#include "internal.h"
+#include "batch.h"
 
 namespace {
 
