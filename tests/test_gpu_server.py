@@ -157,3 +157,26 @@ def test_clustered_solve_matches_oracle():
         assert res[T]["status"] == S.SCGAL_ENOTDONE and res[T]["iterations"] == T
         assert abs(res[T]["objective"] - ref["p_orig"]) <= rtol_p * abs(ref["p_orig"])
         assert abs(res[T]["infeas"] - ref["infeas"]) <= rtol_i * ref["infeas"]
+
+
+@pytest.mark.parametrize("n,kind", [(3000, "real"), (20000, "real"), (33000, "pm1"), (20000, "pm1")])
+def test_served_weight_kinds_match_oracle(n, kind):
+    """Every batched kernel variant against the FP64 oracle after one update
+    (the record of t = 2, where FP32 and FP64 trajectories still coincide):
+    general weights (value arrays in the sliced layout) in a one-block and a
+    clustered instance, +/-1 weights with 32-bit columns (n >= 32767, the sign
+    in bit 31) and with 16-bit columns (sign in bit 15)."""
+    from paper_1912_02949_gb300 import scgal as S
+    from oracle.problems import MaxCutProblem
+    from oracle.sketchycgal import sketchy_cgal
+    S.load()
+    g = W.er_graph(n, 4 * n, seed=11, weights=kind)
+    rp, col, val = g.csr()
+    srv = S.scgal_server_create(1 << 33, 2)
+    res = S.scgal_poll(srv, S.scgal_submit(srv, rp, col, val, g.n, col.size,
+                                           S.scgal_params_default(R=10, T_max=2, tol=0.0, precision=32)), -1)
+    S.scgal_server_destroy(srv)
+    ref = sketchy_cgal(MaxCutProblem(g.n, g.i, g.j, g.w), R=10, T=2, seed=0).history[1]
+    assert res["status"] == S.SCGAL_ENOTDONE and res["iterations"] == 2
+    assert abs(res["objective"] - ref["p_orig"]) <= 1e-5 * abs(ref["p_orig"])
+    assert abs(res["infeas"] - ref["infeas"]) <= 1e-5 * ref["infeas"]
