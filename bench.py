@@ -14,7 +14,9 @@ copies inside the timed region.  The reference arm (`--impl reference`) times
 the FP64 CPU oracle on a bounded sample of the same workload.  `serving` runs
 the first 256 requests of the batched-serving workload (Poisson arrivals at
 200 req/s, MaxCut graphs with n log-uniform in [100, 50000]) through the
-server API: solves/s and p50/p99 latency.
+server API: solves/s and p50/p99 latency.  `phase_retrieval` solves the
+coded-diffraction phase-retrieval workload (n = 2^16, 12 masks) in FP32 and FP64
+and puts its D-matvec against the FP32 ALU roofline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
 """
@@ -167,6 +169,48 @@ def aggregate_serving(local, lat, world: int):
                 "p50_ms": float(np.percentile(allat, 50)), "p99_ms": float(np.percentile(allat, 99)),
                 "converged": sum(p[0]["converged"] for p in parts), "failed": sum(p[0]["failed"] for p in parts),
                 "replicas": world})
+    return out
+
+
+PHASE_DESC = ("phase retrieval SDP with coded diffraction patterns: x in C^n, n=2^16, complex Gaussian; "
+              "L=12 masks uniform on {1,-1,i,-i}; b=|FFT(mask_j.*x)|^2 (d=12n); C=I, alpha=3n, tr X <= alpha; "
+              "R=5, T=1000")
+
+
+def phase_matvec_flops(n: int, L: int) -> float:
+    """Algorithmic FP32 flops of one phase-retrieval D-matvec: 2L complex FFTs of
+    size n at 5 n log2 n each, and the pointwise mask and weight products (6 L n)."""
+    return 2 * L * 5.0 * n * math.log2(n) + 6.0 * L * n
+
+
+def run_phase(S, sm_mhz: float, T: int = 1000, seed: int = SEED):
+    """The phase-retrieval workload solved through the C ABI in FP32 and FP64
+    (T iterations each, host-timed around the synchronous solve), and the FP32
+    D-matvec (three passes of the four-step FFT) timed with CUDA events on its
+    stream against the FP32 ALU roofline (152 SMs x 128 FP32 lanes x 2 flops x
+    the SM clock sampled during the main timed region)."""
+    import workloads as W
+    n, L, R = 1 << 16, 12, 5
+    pd = W.phase_problem(n, L, seed=seed)
+    out = {"desc": PHASE_DESC, "n": n, "L": L, "R": R, "T": T}
+    for prec in (32, 64):
+        h = S.scgal_create_phase(pd.masks, L, n, pd.b, 0.0,
+                                 S.scgal_params_default(R=R, T_max=T, precision=prec, seed=seed))
+        if prec == 32:
+            mv_ms = S.scgal_time_kernel(h, 0, 200)
+        t0 = time.perf_counter()
+        rc, last = S.scgal_solve(h, T)
+        sec = time.perf_counter() - t0
+        h.close()
+        out[f"fp{prec}"] = {"iter_per_s": T / sec, "seconds": sec, "relgap_T": last["relgap"],
+                            "infeas_T": last["infeas"]}
+    flops = phase_matvec_flops(n, L)
+    peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / (mv_ms * 1e-3) / 1e12
+    out["matvec_roofline"] = {"bound": "alu", "kernel": "phase-retrieval D-matvec (k_ph_p1/p2/p3)",
+                              "ms_per_launch": mv_ms, "flops_per_launch": flops, "achieved": achieved,
+                              "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                              "bytes_per_launch": 64 * n, "peak_source": "152 SMs x 128 FP32 lanes x 2 x sampled clock"}
     return out
 
 
@@ -335,6 +379,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=256,
                     help="requests of the batched-serving slice (0: skip the serving leg)")
     ap.add_argument("--serve-slots", type=int, default=152)
+    ap.add_argument("--no-phase", action="store_true", help="skip the phase-retrieval leg")
     ap.add_argument("--profile-serve", type=int, default=0,
                     help="only run K requests of the serving workload with T_max=300 (for profiler captures)")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
@@ -470,6 +515,10 @@ def main():
                 "traffic": profiled_traffic(), "kernel": "k_spmv_step (CSR D-matvec + omega reduction)",
                 "bytes_per_launch": bytes_step, "ms_per_launch": kern["spmv_step"], "peak_source": peak_src}
 
+    phase = None
+    if not args.no_phase:
+        phase = run_phase(S, (clk or {}).get("sm_mhz") or 2070.0)
+
     serving = None
     if args.serve_requests > 0:
         local, lat = run_serving(S, args.serve_requests, args.serve_slots, seed=replica_seed(rank))
@@ -493,7 +542,7 @@ def main():
                 "gpu_launches": args.steps * launches_per_solve(n, T),
                 "clocks": clk, "solve": {"relgap_T": last["relgap"], "infeas_T": last["infeas"],
                                          "objective_T": last["p"], "best_cut": cut, "lambda_top3": list(lam[:3])},
-                "kernels_ms_per_launch": kern, "kernel_share_of_solve": share, "serving": serving, **extra}
+                "kernels_ms_per_launch": kern, "kernel_share_of_solve": share, "serving": serving, "phase_retrieval": phase, **extra}
         if hist32:
             hit = next((r["t"] for r in hist32 if r["relgap"] <= 1e-3 and r["infeas"] <= 1e-3), None)
             line["solve"]["first_t_gap_1e-3"] = hit

@@ -40,25 +40,33 @@ __device__ __forceinline__ V twid(const V* tw, int k, int n, int sign) {
     return w;
 }
 
+// The twiddles exp(-2 pi i k / 2^lg), k < 2^(lg-1), of the length-2^lg
+// transforms, copied from the length-n table into shared memory (n = 2^lg2n).
+template <typename V>
+__device__ __forceinline__ void load_small_twiddles(V* tws, const V* tw, int lg, int lg2n) {
+    for (int k = threadIdx.x; k < (1 << (lg - 1)); k += blockDim.x) tws[k] = tw[k << (lg2n - lg)];
+}
+
 // In-place radix-2 DIT FFTs on `batch` sequences of length 2^lg held in shared
 // memory with element stride es and batch stride bs; input in bit-reversed order.
+// tws: the length-2^lg twiddles in shared memory (load_small_twiddles).
 template <typename V>
-__device__ void smem_fft(V* x, int lg, int batch, int es, int bs, const V* tw, int n, int sign) {
-    const int len = 1 << lg;
-    const int half_total = (len >> 1) * batch;
+__device__ void smem_fft(V* x, int lg, int batch, int es, int bs, const V* tws, int sign) {
+    const int hl = 1 << (lg - 1);
+    const int half_total = hl * batch;
     for (int s = 1; s <= lg; ++s) {
         const int half = 1 << (s - 1);
-        const int tstride = n >> s;   // twiddle exp(sign 2 pi i pos / 2^s) = tw[pos * n / 2^s]
         for (int idx = threadIdx.x; idx < half_total; idx += blockDim.x) {
-            const int b = idx / (len >> 1);
-            const int k = idx - b * (len >> 1);
+            const int b = idx >> (lg - 1);
+            const int k = idx & (hl - 1);
             const int grp = k >> (s - 1);
             const int pos = k & (half - 1);
-            const int i0 = grp * 2 * half + pos;
+            const int i0 = (grp << s) + pos;
             const int i1 = i0 + half;
             V* a0 = x + b * bs + i0 * es;
             V* a1 = x + b * bs + i1 * es;
-            const V w = twid(tw, pos * tstride, n, sign);
+            V w = tws[pos << (lg - s)];   // exp(sign 2 pi i pos / 2^s)
+            if (sign > 0) w.y = -w.y;
             const V u = *a0;
             const V t = CX<V>::mul(*a1, w);
             a0->x = u.x + t.x;
@@ -76,19 +84,22 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ph_p1(KP<V> p, const V* __restrict
     extern __shared__ unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
     const int n = p.c.n, n1 = p.n1, n2 = p.n2, TC = p.ph_tc, lg2 = p.log2;
+    const int ltc = __ffs(TC) - 1;
+    V* tws = sm + n2 * TC;
+    load_small_twiddles(tws, p.twiddle, lg2, p.log2n);
     const int j = blockIdx.y;
     const int k1base = blockIdx.x * TC;
     const V* __restrict__ mask = p.masks + (size_t)j * n;
     for (int idx = threadIdx.x; idx < n2 * TC; idx += blockDim.x) {
-        const int k2 = idx / TC, c = idx - k2 * TC;
+        const int k2 = idx >> ltc, c = idx & (TC - 1);
         const int e = k1base + c + n1 * k2;
         sm[brev(k2, lg2) * TC + c] = CX<V>::mul(x[e], mask[e]);
     }
     __syncthreads();
-    smem_fft<V>(sm, lg2, TC, TC, 1, p.twiddle, n, -1);
+    smem_fft<V>(sm, lg2, TC, TC, 1, tws, -1);
     V* out = p.fftbuf + (size_t)j * n;
     for (int idx = threadIdx.x; idx < n2 * TC; idx += blockDim.x) {
-        const int l2 = idx / TC, c = idx - l2 * TC;
+        const int l2 = idx >> ltc, c = idx & (TC - 1);
         const int k1 = k1base + c;
         out[(size_t)l2 * n1 + k1] = CX<V>::mul(sm[l2 * TC + c], twid(p.twiddle, k1 * l2, n, -1));
     }
@@ -105,19 +116,21 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ph_p2(KP<V> p, const typename VT<V
     const int n = p.c.n, n1 = p.n1, RPB = p.ph_rpb, lg1 = p.log1;
     V* sa = reinterpret_cast<V*>(smraw);
     V* sb = sa + RPB * n1;
+    V* tws = sb + RPB * n1;
+    load_small_twiddles(tws, p.twiddle, lg1, p.log2n);
     const int j = blockIdx.y;
     const int l2base = blockIdx.x * RPB;
     V* buf = p.fftbuf + (size_t)j * n + (size_t)l2base * n1;
     for (int idx = threadIdx.x; idx < RPB * n1; idx += blockDim.x) {
-        const int r = idx / n1, k1 = idx - r * n1;
+        const int r = idx >> lg1, k1 = idx & (n1 - 1);
         sa[r * n1 + brev(k1, lg1)] = buf[idx];
     }
     __syncthreads();
-    smem_fft<V>(sa, lg1, RPB, 1, n1, p.twiddle, n, -1);
+    smem_fft<V>(sa, lg1, RPB, 1, n1, tws, -1);
     if constexpr (MODE == 0) {
         const Rt* wj = w + (size_t)j * n + (size_t)l2base * n1;
         for (int idx = threadIdx.x; idx < RPB * n1; idx += blockDim.x) {
-            const int r = idx / n1, l1 = idx - r * n1;
+            const int r = idx >> lg1, l1 = idx & (n1 - 1);
             const Rt ww = wj[idx];
             V v = sa[idx];
             v.x *= ww;
@@ -125,9 +138,9 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ph_p2(KP<V> p, const typename VT<V
             sb[r * n1 + brev(l1, lg1)] = v;
         }
         __syncthreads();
-        smem_fft<V>(sb, lg1, RPB, 1, n1, p.twiddle, n, +1);
+        smem_fft<V>(sb, lg1, RPB, 1, n1, tws, +1);
         for (int idx = threadIdx.x; idx < RPB * n1; idx += blockDim.x) {
-            const int r = idx / n1, m1 = idx - r * n1;
+            const int r = idx >> lg1, m1 = idx & (n1 - 1);
             buf[idx] = CX<V>::mul(sb[idx], twid(p.twiddle, (l2base + r) * m1, n, +1));
         }
     } else {
@@ -208,6 +221,9 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ph_p3(KP<V> p, const V* __restrict
     extern __shared__ unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
     const int n = p.c.n, n1 = p.n1, n2 = p.n2, TC = p.ph_tc, lg2 = p.log2, L = p.c.L;
+    const int ltc = __ffs(TC) - 1;
+    V* tws = sm + n2 * TC;
+    load_small_twiddles(tws, p.twiddle, lg2, p.log2n);
     const int m1base = blockIdx.x * TC;
     const int g = blockIdx.y;
     const int j0 = g * p.ph_mb, j1 = min(L, j0 + p.ph_mb);
@@ -219,17 +235,17 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ph_p3(KP<V> p, const V* __restrict
         const V* buf = p.fftbuf + (size_t)j * n;
         __syncthreads();
         for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
-            const int l2 = idx / TC, c = idx - l2 * TC;
+            const int l2 = idx >> ltc, c = idx & (TC - 1);
             sm[brev(l2, lg2) * TC + c] = buf[(size_t)l2 * n1 + m1base + c];
         }
         __syncthreads();
-        smem_fft<V>(sm, lg2, TC, TC, 1, p.twiddle, n, +1);
+        smem_fft<V>(sm, lg2, TC, TC, 1, tws, +1);
         const V* mask = p.masks + (size_t)j * n;
 #pragma unroll
         for (int s = 0; s < MAXE; ++s) {
             const int idx = threadIdx.x + s * SCGAL_BS;
             if (idx < nel) {
-                const int m2 = idx / TC, c = idx - m2 * TC;
+                const int m2 = idx >> ltc, c = idx & (TC - 1);
                 const int e = m1base + c + n1 * m2;
                 const V hcon = CX<V>::cmul(mask[e], sm[idx]);   // conj(psi) * H
                 acc[s].x += hcon.x;
@@ -243,7 +259,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ph_p3(KP<V> p, const V* __restrict
     for (int s = 0; s < MAXE; ++s) {
         const int idx = threadIdx.x + s * SCGAL_BS;
         if (idx < nel) {
-            const int m2 = idx / TC, c = idx - m2 * TC;
+            const int m2 = idx >> ltc, c = idx & (TC - 1);
             const int e = m1base + c + n1 * m2;
             V val = acc[s];
             const V xe = x[e];
@@ -288,8 +304,13 @@ __global__ void k_wvec_from_w(KP<V> p, const double* w) {
 }
 
 // ---------------------------------------------------------------------------
-template <typename V> static size_t col_smem(const KP<V>& p) { return sizeof(V) * (size_t)p.n2 * p.ph_tc; }
-template <typename V> static size_t row_smem(const KP<V>& p) { return 2 * sizeof(V) * (size_t)p.n1 * p.ph_rpb; }
+// transform tile, then the length-n2 (columns) or length-n1 (rows) twiddles
+template <typename V> static size_t col_smem(const KP<V>& p) {
+    return sizeof(V) * ((size_t)p.n2 * p.ph_tc + (size_t)(p.n2 / 2 + 1));
+}
+template <typename V> static size_t row_smem(const KP<V>& p) {
+    return sizeof(V) * (2 * (size_t)p.n1 * p.ph_rpb + (size_t)(p.n1 / 2 + 1));
+}
 
 template <typename V>
 static void forward_and_weight(const KP<V>& p, const V* x, const typename VT<V>::R* w, cudaStream_t s) {
