@@ -47,34 +47,66 @@ __device__ __forceinline__ void load_small_twiddles(V* tws, const V* tw, int lg,
     for (int k = threadIdx.x; k < (1 << (lg - 1)); k += blockDim.x) tws[k] = tw[k << (lg2n - lg)];
 }
 
-// In-place radix-2 DIT FFTs on `batch` sequences of length 2^lg held in shared
-// memory with element stride es and batch stride bs; input in bit-reversed order.
+// Stages s0 .. s0+NB-1 (1-based) of an in-place radix-2 DIT FFT on `batch`
+// sequences of length 2^lg in shared memory (element stride es, batch stride
+// bs, input in bit-reversed order).  These stages pair elements whose indices
+// differ only in bits s0-1 .. s0+NB-2, so each work item holds the 2^NB
+// elements that agree in all other bits in registers and runs the NB stages
+// there: one shared-memory round trip and one barrier per NB stages.  Stage s
+// pairs index i0 (bit s-1 clear) with i0 + 2^(s-1), twiddle
+// exp(sign 2 pi i pos / 2^s), pos = i0 mod 2^(s-1): the same butterflies in
+// the same order as one stage at a time.
+template <typename V, int NB>
+__device__ __forceinline__ void fft_stages(V* x, int lg, int s0, int batch, int es, int bs, const V* tws, int sign) {
+    constexpr int P = 1 << NB;
+    const int per_seq = 1 << (lg - NB);
+    const int lowbits = s0 - 1;
+    for (int item = threadIdx.x; item < batch * per_seq; item += blockDim.x) {
+        const int b = item >> (lg - NB);
+        const int r = item & (per_seq - 1);
+        const int low = r & ((1 << lowbits) - 1);
+        const int base = ((r >> lowbits) << (lowbits + NB)) | low;
+        V* xb = x + b * bs;
+        V v[P];
+#pragma unroll
+        for (int t = 0; t < P; ++t) v[t] = xb[(base | (t << lowbits)) * es];
+#pragma unroll
+        for (int st = 0; st < NB; ++st) {
+            const int s = s0 + st;
+            const int half = 1 << (s - 1);
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                if (t & (1 << st)) continue;
+                const int t1 = t | (1 << st);
+                const int pos = (base | (t << lowbits)) & (half - 1);
+                V w = tws[pos << (lg - s)];
+                if (sign > 0) w.y = -w.y;
+                const V u = v[t];
+                const V tt = CX<V>::mul(v[t1], w);
+                v[t].x = u.x + tt.x;
+                v[t].y = u.y + tt.y;
+                v[t1].x = u.x - tt.x;
+                v[t1].y = u.y - tt.y;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < P; ++t) xb[(base | (t << lowbits)) * es] = v[t];
+    }
+    __syncthreads();
+}
+
+// In-place FFTs on `batch` sequences of length 2^lg held in shared memory with
+// element stride es and batch stride bs; input in bit-reversed order.
 // tws: the length-2^lg twiddles in shared memory (load_small_twiddles).
 template <typename V>
 __device__ void smem_fft(V* x, int lg, int batch, int es, int bs, const V* tws, int sign) {
-    const int hl = 1 << (lg - 1);
-    const int half_total = hl * batch;
-    for (int s = 1; s <= lg; ++s) {
-        const int half = 1 << (s - 1);
-        for (int idx = threadIdx.x; idx < half_total; idx += blockDim.x) {
-            const int b = idx >> (lg - 1);
-            const int k = idx & (hl - 1);
-            const int grp = k >> (s - 1);
-            const int pos = k & (half - 1);
-            const int i0 = (grp << s) + pos;
-            const int i1 = i0 + half;
-            V* a0 = x + b * bs + i0 * es;
-            V* a1 = x + b * bs + i1 * es;
-            V w = tws[pos << (lg - s)];   // exp(sign 2 pi i pos / 2^s)
-            if (sign > 0) w.y = -w.y;
-            const V u = *a0;
-            const V t = CX<V>::mul(*a1, w);
-            a0->x = u.x + t.x;
-            a0->y = u.y + t.y;
-            a1->x = u.x - t.x;
-            a1->y = u.y - t.y;
+    for (int s0 = 1; s0 <= lg; s0 += 4) {
+        switch (min(4, lg - s0 + 1)) {
+            case 4: fft_stages<V, 4>(x, lg, s0, batch, es, bs, tws, sign); break;
+            case 3: fft_stages<V, 3>(x, lg, s0, batch, es, bs, tws, sign); break;
+            case 2: fft_stages<V, 2>(x, lg, s0, batch, es, bs, tws, sign); break;
+            default: fft_stages<V, 1>(x, lg, s0, batch, es, bs, tws, sign); break;
         }
-        __syncthreads();
     }
 }
 
