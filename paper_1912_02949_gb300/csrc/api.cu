@@ -14,6 +14,10 @@
 
 #include "batch.h"
 
+namespace scgal {
+template <typename V> int prepare_phase_kernels(const KP<V>& p);   // k_phase.cu
+}
+
 using namespace scgal;
 
 namespace {
@@ -454,6 +458,7 @@ int phase_build(scgal_ctx* h, const double* masks, const double* b) {
     if (p3blocks > h->grid_elem) h->grid_spmv = p3blocks;
     const int p2blocks = (p.n2 / p.ph_rpb) * L;
     if (p2blocks > h->grid_spmv) h->grid_spmv = p2blocks;
+    if (prepare_phase_kernels<V>(p)) return set_err(h, SCGAL_ECUDA, "phase-retrieval kernels: shared memory");
     return setup_state<V>(h);
 }
 

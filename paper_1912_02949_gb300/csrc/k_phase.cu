@@ -350,6 +350,23 @@ static void forward_and_weight(const KP<V>& p, const V* x, const typename VT<V>:
     k_ph_p2<V, 0><<<dim3(p.n2 / p.ph_rpb, p.c.L), SCGAL_BS, row_smem(p), s>>>(p, w);
 }
 
+// Raises the passes' dynamic shared-memory limit to what this handle's tiles
+// need (above 48 KB for the wider tiles); called once per handle, before any
+// launch or capture.
+template <typename V> int prepare_phase_kernels(const KP<V>& p) {
+    const int cs = (int)col_smem(p), rs = (int)row_smem(p);
+    cudaError_t e = cudaFuncSetAttribute(k_ph_p1<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ph_p3<V, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ph_p3<V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ph_p2<V, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ph_p2<V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SCGAL_ECUDA;
+    }
+    return SCGAL_OK;
+}
+
 template <typename V> void launch_phase_step(const KP<V>& p, int i, cudaStream_t s) {
     const V* x = p.basis + (size_t)i * p.ldb;
     // the column and row passes skip nothing on breakdown; only their cost is wasted
@@ -389,6 +406,7 @@ void phase_perm(const double* in, double* out, long long d, int n, int n1, int n
 }
 
 #define INST(V)                                                                                           \
+    template int prepare_phase_kernels<V>(const KP<V>&);                                                  \
     template void launch_phase_step<V>(const KP<V>&, int, cudaStream_t);                                  \
     template void launch_phase_update<V>(const KP<V>&, int, cudaStream_t);                                \
     template void launch_apply_D_phase<V>(const KP<V>&, const V*, V*, const typename VT<V>::R*, cudaStream_t); \
