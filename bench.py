@@ -363,6 +363,20 @@ def profile_solve(T: int):
     h.close()
 
 
+def profile_phase(T: int):
+    """One untimed FP32 solve of the phase-retrieval workload (for ncu captures)."""
+    import workloads as W
+    from paper_1912_02949_gb300 import scgal as S
+    S.load()
+    n, L = 1 << 16, 12
+    pd = W.phase_problem(n, L, seed=SEED)
+    h = S.scgal_create_phase(pd.masks, L, n, pd.b, 0.0, S.scgal_params_default(R=5, T_max=T, precision=32, seed=SEED))
+    t0 = time.perf_counter()
+    rc, last = S.scgal_solve(h, T)
+    print(json.dumps({"T": T, "seconds": time.perf_counter() - t0, "relgap": last["relgap"]}))
+    h.close()
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -386,6 +400,8 @@ def main():
     ap.add_argument("--cpu-reps", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--profile-solve", action="store_true",
                     help="one untimed FP32 solve of T iterations of the workload (for ncu captures)")
+    ap.add_argument("--profile-phase", action="store_true",
+                    help="one untimed FP32 solve of T iterations of the phase-retrieval workload (for ncu captures)")
     args = ap.parse_args()
     if args.cpu_sample:
         print(json.dumps(cpu_sample(args.cpu_sample, args.cpu_reps)))
@@ -395,6 +411,9 @@ def main():
         return
     if args.profile_solve:
         profile_solve(args.T)
+        return
+    if args.profile_phase:
+        profile_phase(args.T)
         return
     if args.profile_serve:
         from paper_1912_02949_gb300 import scgal as S
