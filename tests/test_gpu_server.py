@@ -180,3 +180,27 @@ def test_served_weight_kinds_match_oracle(n, kind):
     assert res["status"] == S.SCGAL_ENOTDONE and res["iterations"] == 2
     assert abs(res["objective"] - ref["p_orig"]) <= 1e-5 * abs(ref["p_orig"])
     assert abs(res["infeas"] - ref["infeas"]) <= 1e-5 * ref["infeas"]
+
+
+def test_graph_path_requests_share_rounds(S):
+    """Requests the batched engine does not take -- FP64, and n above its
+    shared-memory limit -- run on their handles' own graphs in the same rounds
+    as batched ones; every result is identical alone and mixed."""
+    specs = [(1200, "unit", 32), (2500, "pm1", 64), (60000, "unit", 32), (900, "unit", 32), (20000, "unit", 32)]
+    reqs = []
+    for k, (n, kind, prec) in enumerate(specs):
+        g = W.er_graph(n, 4 * n, seed=200 + k, weights=kind)
+        rp, col, val = g.csr()
+        reqs.append((k, g, rp, col, val if kind != "unit" else None, prec))
+
+    def prm(k, prec):
+        return S.scgal_params_default(R=10, T_max=40, tol=0.0, precision=prec, seed=3, instance=k)
+
+    srv = S.scgal_server_create(1 << 34, 8)
+    tickets = [S.scgal_submit(srv, rp, col, val, g.n, col.size, prm(k, prec)) for k, g, rp, col, val, prec in reqs]
+    mixed = [S.scgal_poll(srv, t, -1) for t in tickets]
+    for (k, g, rp, col, val, prec), res in zip(reqs, mixed):
+        alone = S.scgal_poll(srv, S.scgal_submit(srv, rp, col, val, g.n, col.size, prm(k, prec)), -1)
+        assert res["status"] == S.SCGAL_ENOTDONE and res["iterations"] == 40
+        assert _result_fields(res) == _result_fields(alone)
+    S.scgal_server_destroy(srv)
