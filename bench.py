@@ -16,7 +16,8 @@ the first 256 requests of the batched-serving workload (Poisson arrivals at
 200 req/s, MaxCut graphs with n log-uniform in [100, 50000]) through the
 server API: solves/s and p50/p99 latency.  `phase_retrieval` solves the
 coded-diffraction phase-retrieval workload (n = 2^16, 12 masks) in FP32 and FP64
-and puts its D-matvec against the FP32 ALU roofline.
+and puts its D-matvec against the FP32 ALU roofline.  `large_maxcut` solves the
+n = 2^23 torus MaxCut (T = 1000) from HBM-resident CSR.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
 """
@@ -214,6 +215,37 @@ def run_phase(S, sm_mhz: float, T: int = 1000, seed: int = SEED):
     return out
 
 
+LARGE_DESC = ("large MaxCut SDP: 2048 x 4096 torus plus 10% long-range edges (n = 2^23), +/-1 weights, "
+              "R=10, T=1000, FP32 sketch and basis on one GPU, FP64 reconstruction and integer rounding")
+
+
+def run_large(S, T: int = 1000, seed: int = SEED):
+    """The n = 2^23 torus MaxCut solved through the C ABI from HBM-resident CSR
+    (create, T iterations, reconstruction and rounding; host-timed around the
+    synchronous calls)."""
+    import torch
+    import workloads as W
+    g = W.config_graph("torus2p23", seed=seed)
+    rp, col, val = g.csr()
+    dev = torch.device("cuda", 0)
+    d_rp, d_col, d_w = (torch.from_numpy(a).to(dev) for a in (rp, col, val))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = S.scgal_create_maxcut(d_rp, d_col, d_w, g.n, int(col.size), 0.0,
+                              S.scgal_params_default(R=R, T_max=T, precision=32, seed=seed))
+    t1 = time.perf_counter()
+    rc, last = S.scgal_solve(h, T)
+    t2 = time.perf_counter()
+    _, lam, _, cut = S.scgal_reconstruct(h)
+    t3 = time.perf_counter()
+    info = S.scgal_get_info(h)
+    h.close()
+    return {"desc": LARGE_DESC, "n": g.n, "nnz": int(col.size), "T": T, "iter_per_s": T / (t2 - t1),
+            "create_s": t1 - t0, "solve_s": t2 - t1, "reconstruct_s": t3 - t2, "relgap_T": last["relgap"],
+            "infeas_T": last["infeas"], "objective_T": last["p"], "best_cut": int(cut),
+            "lambda_max": float(lam[0]), "device_bytes": int(info["device_bytes"])}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -394,6 +426,7 @@ def main():
                     help="requests of the batched-serving slice (0: skip the serving leg)")
     ap.add_argument("--serve-slots", type=int, default=152)
     ap.add_argument("--no-phase", action="store_true", help="skip the phase-retrieval leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the n = 2^23 torus MaxCut leg")
     ap.add_argument("--profile-serve", type=int, default=0,
                     help="only run K requests of the serving workload with T_max=300 (for profiler captures)")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
@@ -534,6 +567,10 @@ def main():
                 "traffic": profiled_traffic(), "kernel": "k_spmv_step (CSR D-matvec + omega reduction)",
                 "bytes_per_launch": bytes_step, "ms_per_launch": kern["spmv_step"], "peak_source": peak_src}
 
+    large = None
+    if not args.no_large and args.workload == "er2p20":
+        large = run_large(S)
+
     phase = None
     if not args.no_phase:
         phase = run_phase(S, (clk or {}).get("sm_mhz") or 2070.0)
@@ -561,7 +598,7 @@ def main():
                 "gpu_launches": args.steps * launches_per_solve(n, T),
                 "clocks": clk, "solve": {"relgap_T": last["relgap"], "infeas_T": last["infeas"],
                                          "objective_T": last["p"], "best_cut": cut, "lambda_top3": list(lam[:3])},
-                "kernels_ms_per_launch": kern, "kernel_share_of_solve": share, "serving": serving, "phase_retrieval": phase, **extra}
+                "kernels_ms_per_launch": kern, "kernel_share_of_solve": share, "serving": serving, "phase_retrieval": phase, "large_maxcut": large, **extra}
         if hist32:
             hit = next((r["t"] for r in hist32 if r["relgap"] <= 1e-3 and r["infeas"] <= 1e-3), None)
             line["solve"]["first_t_gap_1e-3"] = hit
