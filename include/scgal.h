@@ -116,6 +116,7 @@ void scgal_params_default(scgal_params* p);
  *       is +1 or -1 the signs are packed into the column indices (4 bytes per
  *       stored entry).
  *   alpha: trace bound; <= 0 selects alpha = n.
+ *   params->R <= n (the n x R sketch of an n x n matrix; checked: SCGAL_EINVAL).
  * On success *out is a new handle at t = 1 (z = y = 0, S = 0). */
 int scgal_create_maxcut(const int32_t* row_ptr, const int32_t* col, const double* w,
                         int32_t n, int64_t nnz, double alpha,
@@ -127,7 +128,7 @@ int scgal_create_maxcut(const int32_t* row_ptr, const int32_t* col, const double
  *   masks: L*n complex128 values as interleaved (re, im) doubles, mask-major;
  *          every |psi_j[k]| must be 1 (the closed form ||A|| = n sqrt(L) of the
  *          scaling needs it; checked: SCGAL_EINVAL).
- *   L >= 1; n a power of two, 16 <= n <= 2^20.
+ *   L >= 1; n a power of two, 16 <= n <= 2^20; params->R <= n (SCGAL_EINVAL).
  *   b: L*n doubles.   alpha: <= 0 selects alpha = 3n (Section 7.3.3).
  * The problem is complex Hermitian; vectors are complex64 (precision 32) or
  * complex128 (precision 64). */

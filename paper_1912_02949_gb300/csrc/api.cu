@@ -1076,6 +1076,7 @@ int scgal_create_maxcut(const int32_t* row_ptr, const int32_t* col, const double
     *out = nullptr;
     if (!row_ptr || (nnz > 0 && !col) || n < 2 || nnz < 0 || nnz >= (1ll << 31)) return SCGAL_EINVAL;
     if (check_params(params)) return SCGAL_EINVAL;
+    if (params->R > n) return SCGAL_EINVAL;   // the n x R sketch of an n x n matrix
     scgal_ctx* h = new_ctx(params, KIND_MAXCUT);
     h->cplx = 0;
     h->n = n;
@@ -1100,6 +1101,7 @@ int scgal_create_phase(const double* masks, int32_t L, int32_t n, const double* 
     *out = nullptr;
     if (!masks || !b || L < 1 || n < 16 || n > (1 << 20) || (n & (n - 1))) return SCGAL_EINVAL;
     if (check_params(params)) return SCGAL_EINVAL;
+    if (params->R > n) return SCGAL_EINVAL;   // the n x R sketch of an n x n matrix
     scgal_ctx* h = new_ctx(params, KIND_PHASE);
     h->cplx = 1;
     h->n = n;

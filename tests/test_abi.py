@@ -75,5 +75,13 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert lib.scgal_create_maxcut(None, None, None, 1, 0, 0.0, ctypes.byref(p), ctypes.byref(h)) == S.SCGAL_EINVAL
     bad = S.scgal_params_default(R=0)
     assert lib.scgal_create_phase(None, 12, 64, None, 0.0, ctypes.byref(bad), ctypes.byref(h)) == S.SCGAL_EINVAL
+    # a sketch rank above n is rejected before any CUDA call
+    rp = (ctypes.c_int32 * 3)(0, 1, 2)
+    cl = (ctypes.c_int32 * 2)(1, 0)
+    big = S.scgal_params_default(R=3)
+    assert lib.scgal_create_maxcut(rp, cl, None, 2, 2, 0.0, ctypes.byref(big), ctypes.byref(h)) == S.SCGAL_EINVAL
+    m = (ctypes.c_double * 64)()
+    big = S.scgal_params_default(R=17)
+    assert lib.scgal_create_phase(m, 1, 16, m, 0.0, ctypes.byref(big), ctypes.byref(h)) == S.SCGAL_EINVAL
     assert lib.scgal_strerror(S.SCGAL_ENUMERIC).decode() == "numerical failure"
     assert lib.scgal_step(None, None) == S.SCGAL_EINVAL

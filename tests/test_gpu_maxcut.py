@@ -84,7 +84,7 @@ def test_apply_D_edge_cases(S, prec):
     # empty graph (C = 0): D = diag(w);  smallest instance n = 2
     for n, m in ((50, 0), (2, 1)):
         g2 = W.er_graph(n, m, seed=0, weights="unit")
-        h2 = _handle(S, g2, prec)
+        h2 = _handle(S, g2, prec, R=min(10, n))
         p2 = MaxCutProblem(g2.n, g2.i, g2.j, g2.w)
         x2 = np.arange(1.0, n + 1)
         w2 = np.cos(np.arange(n))
@@ -92,7 +92,7 @@ def test_apply_D_edge_cases(S, prec):
 
 
 def test_malformed_csr_is_rejected(S):
-    p = S.scgal_params_default(T_max=10)
+    p = S.scgal_params_default(T_max=10, R=2)
     rp = np.array([0, 2, 1, 3], dtype=np.int32)          # decreasing row pointer
     col = np.array([1, 2, 0], dtype=np.int32)
     with pytest.raises(S.ScgalError) as e:

@@ -204,3 +204,47 @@ def test_graph_path_requests_share_rounds(S):
         assert res["status"] == S.SCGAL_ENOTDONE and res["iterations"] == 40
         assert _result_fields(res) == _result_fields(alone)
     S.scgal_server_destroy(srv)
+
+
+@pytest.mark.parametrize("n,m,R", [(2, 1, 2), (50, 0, 10), (300, 900, 1), (300, 900, 5), (300, 900, 16)])
+def test_batched_edge_cases_match_oracle(n, m, R):
+    """Batched solves at the edges of the engine: the smallest graph, a graph
+    without edges (every slice of width 0; C = 0, Eq. 7.1 leaves it unscaled),
+    and sketch ranks 1, 5 and 16 (the Ritz step's accumulator widths), against
+    the FP64 oracle after one update.  Without edges D_1 = -beta b I is a
+    multiple of the identity, every vector is a minimum eigenvector and the one
+    Lanczos returns is decided by rounding (the oracle's own infeasibility
+    differs between x86 and Arm), so only the exact objective 0 is compared."""
+    from paper_1912_02949_gb300 import scgal as S
+    from oracle.problems import MaxCutProblem
+    from oracle.sketchycgal import sketchy_cgal
+    S.load()
+    g = W.er_graph(n, m, seed=21, weights="unit")
+    rp, col, _ = g.csr()
+    srv = S.scgal_server_create(1 << 32, 2)
+    res = S.scgal_poll(srv, S.scgal_submit(srv, rp, col, None, g.n, col.size,
+                                           S.scgal_params_default(R=R, T_max=2, tol=0.0, precision=32)), -1)
+    S.scgal_server_destroy(srv)
+    ref = sketchy_cgal(MaxCutProblem(g.n, g.i, g.j, g.w), R=R, T=2, seed=0).history[1]
+    assert res["status"] == S.SCGAL_ENOTDONE and res["iterations"] == 2
+    assert abs(res["objective"] - ref["p_orig"]) <= 1e-5 * max(abs(ref["p_orig"]), 1.0)
+    if m == 0:
+        assert res["objective"] == 0.0 and np.isfinite(res["infeas"])
+    else:
+        assert abs(res["infeas"] - ref["infeas"]) <= 1e-5 * max(ref["infeas"], 1e-3)
+
+
+def test_batched_solve_converges_early():
+    """A loose tolerance: the stopping rule (Eq. E.1) ends the batched solve
+    before T_max and the result carries status OK and the iterations run."""
+    from paper_1912_02949_gb300 import scgal as S
+    S.load()
+    g = W.er_graph(2000, 8000, seed=22, weights="unit")
+    rp, col, _ = g.csr()
+    srv = S.scgal_server_create(1 << 32, 2)
+    res = S.scgal_poll(srv, S.scgal_submit(srv, rp, col, None, g.n, col.size,
+                                           S.scgal_params_default(R=10, T_max=3000, tol=5e-2, precision=32)), -1)
+    S.scgal_server_destroy(srv)
+    assert res["status"] == S.SCGAL_OK
+    assert 1 <= res["iterations"] < 3000
+    assert res["relgap"] <= 5e-2 and res["infeas"] <= 5e-2
