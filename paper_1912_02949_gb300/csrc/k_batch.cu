@@ -1321,9 +1321,11 @@ int launch_batch(BatchLaunch* L, const void* d_slots, const int* d_active, const
         max_clusters = std::max(1, std::min(mc, sms / CL));
         ready = 1;
     }
-    // Blocks: clustered instances first (CL SMs each), in proportion to the
-    // SMs the two kinds of instance would occupy; every launched variant gets
-    // at least one block (cluster).  Within a variant, instances beyond its
+    // Blocks: the one-block (small) instances first -- one SM each, as many as
+    // the SMs allow while at least one cluster keeps running -- since the
+    // shortest solves first keep the median latency down at little cost to the
+    // rest; the clusters take the remaining SMs.  Every launched variant gets
+    // at least one block (cluster); within a variant, instances beyond its
     // blocks share them in time slices of the round.  BATCH_RESERVE_SMS stay
     // free for the kernels that set up and retire solves while a round runs.
     const int avail = std::max(CL + 1, sms - BATCH_RESERVE_SMS);
@@ -1331,9 +1333,8 @@ int launch_batch(BatchLaunch* L, const void* d_slots, const int* d_active, const
     for (int v = 0; v < BATCH_NVAR; ++v) (clustered(v) ? ncl : nsg) += std::max(0, counts[v]);
     int cl_budget = 0;
     if (ncl > 0) {
-        const double want = (double)ncl * CL;
-        const double share = nsg > 0 ? avail * want / (want + (double)nsg) : (double)avail;
-        cl_budget = std::max(1, std::min<int>(max_clusters, (int)std::min<double>((double)ncl, share / CL)));
+        const int left = avail - (int)std::min<long long>(nsg, avail - CL);
+        cl_budget = std::max(1, std::min<int>(max_clusters, (int)std::min<long long>(ncl, left / CL)));
     }
     const int sg_budget = std::max(1, avail - CL * cl_budget);
     // d_ctl: BATCH_NVAR work counters, then the round's deadline (8-byte aligned)
