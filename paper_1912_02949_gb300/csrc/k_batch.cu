@@ -676,7 +676,7 @@ __device__ __forceinline__ void csum(const double (&blk)[NV], double (&out)[NV],
 // Lanczos (as b_lanczos).  Returns 0, 1 on breakdown (rho == 0), 2 on a non-finite value.
 template <bool NARROW, int WK>
 __device__ __forceinline__ int c_lanczos(const BatchSlot& B, int q, ClCtx& cx) {
-    constexpr int U = 8;
+    constexpr int U4 = 1;
     cg::cluster_group cl = cg::this_cluster();
     const KP<float>& p = B.p;
     DevScalars* sc = p.sc;
@@ -711,27 +711,46 @@ __device__ __forceinline__ int c_lanczos(const BatchSlot& B, int q, ClCtx& cx) {
         const float* __restrict__ Wm = p.basis + (size_t)(i > 0 ? i - 1 : i) * ldb;
         float* __restrict__ Wn = p.basis + (size_t)(i + 1) * ldb;
         float acc[1] = {0.f};
-        for (int base = cx.lo + threadIdx.x; base < cx.hi; base += BT * U) {
-            float wm[U], yy[U], xx[U];
+        // groups of four rows (lo is a multiple of 4; the rows of a basis vector
+        // and of x start 16-byte aligned), then the ragged end of the last block
+        const int g_lo = cx.lo >> 2, g_hi = cx.hi >> 2;
+        const float4* Wm4 = reinterpret_cast<const float4*>(Wm);
+        float4* Wn4 = reinterpret_cast<float4*>(Wn);
+        const float4* y4 = reinterpret_cast<const float4*>(p.ybuf);
+        const float4* x4 = reinterpret_cast<const float4*>(xs);
+        for (int g0 = g_lo + (int)threadIdx.x; g0 < g_hi; g0 += BT * U4) {
+            float4 wm[U4], yy[U4], xx[U4];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int r = base + u * BT;
-                const bool in = r < cx.hi;
-                wm[u] = in ? Wm[r] : 0.f;        // this block's rows of W_{i-1}: written by this block
-                yy[u] = in ? __ldcg(p.ybuf + r) : 0.f;
-                xx[u] = in ? xs[r] : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int r = base + u * BT;
-                if (r < cx.hi) {
-                    const float w = fmaf(a, yy[u], fmaf(b, xx[u], c * wm[u]));
-                    Wn[r] = w;
-#pragma unroll
-                    for (int cc = 0; cc < CL; ++cc) peer[cc][r] = w;   // every block's copy of x
-                    acc[0] += w * w;
+            for (int u = 0; u < U4; ++u) {
+                const int g = g0 + u * BT;
+                if (g < g_hi) {
+                    wm[u] = Wm4[g];                 // this block's rows of W_{i-1}: written by this block
+                    yy[u] = __ldcg(y4 + g);
+                    xx[u] = x4[g];
                 }
             }
+#pragma unroll
+            for (int u = 0; u < U4; ++u) {
+                const int g = g0 + u * BT;
+                if (g < g_hi) {
+                    float4 w;
+                    w.x = fmaf(a, yy[u].x, fmaf(b, xx[u].x, c * wm[u].x));
+                    w.y = fmaf(a, yy[u].y, fmaf(b, xx[u].y, c * wm[u].y));
+                    w.z = fmaf(a, yy[u].z, fmaf(b, xx[u].z, c * wm[u].z));
+                    w.w = fmaf(a, yy[u].w, fmaf(b, xx[u].w, c * wm[u].w));
+                    Wn4[g] = w;
+#pragma unroll
+                    for (int cc = 0; cc < CL; ++cc) reinterpret_cast<float4*>(peer[cc])[g] = w;   // every block's x
+                    acc[0] += w.x * w.x + w.y * w.y + w.z * w.z + w.w * w.w;
+                }
+            }
+        }
+        for (int r = 4 * g_hi + (int)threadIdx.x; r < cx.hi; r += BT) {
+            const float w = fmaf(a, __ldcg(p.ybuf + r), fmaf(b, xs[r], c * Wm[r]));
+            Wn[r] = w;
+#pragma unroll
+            for (int cc = 0; cc < CL; ++cc) peer[cc][r] = w;
+            acc[0] += w * w;
         }
         double Rb[1], RR[1];
         bsum<1>(acc, Rb);
