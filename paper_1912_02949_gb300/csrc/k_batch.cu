@@ -619,11 +619,16 @@ k_batch(const BatchSlot* __restrict__ slots, const int* __restrict__ active, int
 // the D-matvec over its share of the slices (warp gw of the cluster's CL * NW
 // warps takes slices gw, gw + CL NW, ...), writing D x to global memory.  Each
 // block owns a contiguous range of rows [lo, hi) for the element-wise steps
-// (Lanczos update, Ritz vector, z / sketch update, dual step) and writes its
-// new entries of x into every block's shared memory (distributed shared
-// memory).  Every cluster barrier is preceded by a memory fence (csync).  Sums: each block's total goes to block 0's shared memory, a
-// cluster barrier, every block adds the CL totals in rank order (so all blocks
-// hold identical totals and take identical decisions), a second barrier.  Global data that
+// (Lanczos update, Ritz vector, z / sketch update, dual step); its new entries
+// of x go to global memory (the new basis vector, or vbuf for the Ritz vector)
+// and, after the next cluster barrier, every block copies the other blocks'
+// rows from L2 into its own shared memory.  Blocks never store into one
+// another's shared memory: the only distributed-shared-memory accesses are
+// reads, after a barrier, of values written before it (the sums' per-block
+// totals).  Every cluster barrier is preceded by a memory fence (csync).
+// Sums: each block's total goes to its own shared memory, a cluster barrier,
+// every block reads and adds the CL totals in rank order (so all blocks hold
+// identical totals and take identical decisions), a second barrier.  Global data that
 // another block wrote is read through L2 (__ldcg).  Block 0 alone writes the
 // instance's scalars and runs the tridiagonal solve.
 constexpr int CL = 4;
@@ -632,7 +637,7 @@ constexpr int BATCH_NMIN_CL = 16384;             // smallest n served by a clust
 constexpr size_t BATCH_SMEM_CL = sizeof(float) * (size_t)LOFF + TSM_BYTES;   // x, then the tridiagonal scratch
 static_assert(BATCH_NMIN_CL <= BATCH_NMAX_Y + 1, "one-block instances keep D x in shared memory");
 
-__shared__ double b_cred[2][CL * RED_NV];       // per-block totals, in block 0 (two alternating sets)
+__shared__ double b_cred[2][RED_NV];            // this block's totals for the cluster sums (two alternating sets)
 
 // Cluster barrier with every earlier write of this thread made visible first.
 // (The barrier alone did not order the blocks' writes here: without the fence,
@@ -654,16 +659,14 @@ __device__ __forceinline__ void csum(const double (&blk)[NV], double (&out)[NV],
     cg::cluster_group cl = cg::this_cluster();
     double* buf = &b_cred[cx.par][0];
     if (threadIdx.x == 0) {
-        double* dst = cl.map_shared_rank(buf, 0);
 #pragma unroll
-        for (int k = 0; k < NV; ++k) dst[cx.rank * NV + k] = blk[k];
+        for (int k = 0; k < NV; ++k) buf[k] = blk[k];   // this block's totals, in its own shared memory
     }
     csync();                                     // also publishes every block's earlier writes
     double* res = b_red + NW * RED_NV;
     if (threadIdx.x < NV) {
-        const double* src = cl.map_shared_rank(buf, 0);
         double t = 0.0;
-        for (int c = 0; c < CL; ++c) t += src[c * NV + threadIdx.x];
+        for (int c = 0; c < CL; ++c) t += cl.map_shared_rank(buf, c)[threadIdx.x];   // rank order
         res[threadIdx.x] = t;
     }
     __syncthreads();
@@ -683,9 +686,6 @@ __device__ __forceinline__ int c_lanczos(const BatchSlot& B, int q, ClCtx& cx) {
     const int n = p.c.n;
     const size_t ldb = (size_t)p.ldb;
     float* xs = b_smem;
-    float* peer[CL];
-#pragma unroll
-    for (int c = 0; c < CL; ++c) peer[c] = cl.map_shared_rank(xs, c);
     const bool lead = cx.rank == 0 && threadIdx.x == 0;
     for (int r = threadIdx.x; r < n; r += BT) xs[r] = __ldcg(p.basis + r);   // W_0, written by all blocks
     __syncthreads();
@@ -717,7 +717,7 @@ __device__ __forceinline__ int c_lanczos(const BatchSlot& B, int q, ClCtx& cx) {
         const float4* Wm4 = reinterpret_cast<const float4*>(Wm);
         float4* Wn4 = reinterpret_cast<float4*>(Wn);
         const float4* y4 = reinterpret_cast<const float4*>(p.ybuf);
-        const float4* x4 = reinterpret_cast<const float4*>(xs);
+        float4* x4 = reinterpret_cast<float4*>(xs);
         for (int g0 = g_lo + (int)threadIdx.x; g0 < g_hi; g0 += BT * U4) {
             float4 wm[U4], yy[U4], xx[U4];
 #pragma unroll
@@ -739,8 +739,7 @@ __device__ __forceinline__ int c_lanczos(const BatchSlot& B, int q, ClCtx& cx) {
                     w.z = fmaf(a, yy[u].z, fmaf(b, xx[u].z, c * wm[u].z));
                     w.w = fmaf(a, yy[u].w, fmaf(b, xx[u].w, c * wm[u].w));
                     Wn4[g] = w;
-#pragma unroll
-                    for (int cc = 0; cc < CL; ++cc) reinterpret_cast<float4*>(peer[cc])[g] = w;   // every block's x
+                    x4[g] = w;
                     acc[0] += w.x * w.x + w.y * w.y + w.z * w.z + w.w * w.w;
                 }
             }
@@ -748,13 +747,15 @@ __device__ __forceinline__ int c_lanczos(const BatchSlot& B, int q, ClCtx& cx) {
         for (int r = 4 * g_hi + (int)threadIdx.x; r < cx.hi; r += BT) {
             const float w = fmaf(a, __ldcg(p.ybuf + r), fmaf(b, xs[r], c * Wm[r]));
             Wn[r] = w;
-#pragma unroll
-            for (int cc = 0; cc < CL; ++cc) peer[cc][r] = w;
+            xs[r] = w;
             acc[0] += w * w;
         }
         double Rb[1], RR[1];
         bsum<1>(acc, Rb);
-        csum<1>(Rb, RR, cx);                     // every block's x complete after this barrier
+        csum<1>(Rb, RR, cx);                     // every block's rows of W_{i+1} visible after this barrier
+        for (int r = threadIdx.x; r < n; r += BT)
+            if (r < cx.lo || r >= cx.hi) xs[r] = __ldcg(Wn + r);
+        __syncthreads();
         const double rho = sqrt(RR[0]);
         if (rho == 0.0 || !isfinite(rho)) {
             if (lead) {
@@ -789,9 +790,6 @@ __device__ __forceinline__ bool c_ritz(const BatchSlot& B, ClCtx& cx, double (&t
     const int k = __ldcg(&sc->k), R = p.c.R;
     const size_t ldb = (size_t)p.ldb;
     float* cf = b_smem + LOFF;
-    float* peer[CL];
-#pragma unroll
-    for (int c = 0; c < CL; ++c) peer[c] = cl.map_shared_rank(b_smem, c);
     for (int j = threadIdx.x; j < k; j += BT) cf[j] = (float)__ldcg(p.coef + j);
     __syncthreads();
     float acc[NV];
@@ -826,8 +824,8 @@ __device__ __forceinline__ bool c_ritz(const BatchSlot& B, ClCtx& cx, double (&t
         for (int u = 0; u < U; ++u) {
             const int r = base + u * BT;
             if (r < cx.hi) {
-#pragma unroll
-                for (int cc = 0; cc < CL; ++cc) peer[cc][r] = v[u];
+                b_smem[r] = v[u];
+                p.vbuf[r] = v[u];
                 acc[0] += v[u] * v[u];
                 const float* om = p.Omega + (size_t)r * R;
 #pragma unroll
@@ -838,7 +836,10 @@ __device__ __forceinline__ bool c_ritz(const BatchSlot& B, ClCtx& cx, double (&t
     }
     double blk[NV], t[NV];
     bsum<NV>(acc, blk);
-    csum<NV>(blk, t, cx);                        // every block's x holds all of v after this barrier
+    csum<NV>(blk, t, cx);                        // every block's rows of v visible after this barrier
+    for (int r = threadIdx.x; r < p.c.n; r += BT)
+        if (r < cx.lo || r >= cx.hi) b_smem[r] = __ldcg(p.vbuf + r);
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i < NV; ++i) tot[i] = t[i];
     if (cx.rank == 0 && threadIdx.x == 0) {
