@@ -484,17 +484,20 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def params(prec, tol=0.0):
-        return S.scgal_params_default(R=R, T_max=T, precision=prec, seed=replica_seed(rank), tol=tol, device=local)
+    def params(prec, tol=0.0, omega=0):
+        return S.scgal_params_default(R=R, T_max=T, precision=prec, seed=replica_seed(rank), tol=tol, device=local,
+                                      omega=omega)
 
-    def solve(prec, host=False, tol=0.0, keep=False):
+    def solve(prec, host=False, tol=0.0, keep=False, omega=0):
         """One full solve; returns (ms, last record, best cut, lambda, handle or None)."""
         bufs = (rp_h, col_h, w_h, U_h) if host else (d_rp, d_col, d_w, U_dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h = S.scgal_create_maxcut(bufs[0], bufs[1], bufs[2], n, nnz, 0.0, params(prec, tol))
+        h = S.scgal_create_maxcut(bufs[0], bufs[1], bufs[2], n, nnz, 0.0, params(prec, tol, omega))
         S.scgal_set_stream(h, stream.cuda_stream)
+        if keep:
+            solve.device_bytes = S.scgal_get_info(h)["device_bytes"]
         rc, last = S.scgal_solve(h, T)
         U, lam, err, cut = S.scgal_reconstruct(h, U=bufs[3])
         e1.record(stream)
@@ -546,6 +549,18 @@ def main():
     e2e = {"value": T / (ms_e2e / 1000.0), "unit": "iter/s",
            "h2d_bytes_per_step": 4 * (n + 1) + 4 * nnz + 8 * nnz,
            "d2h_bytes_per_step": 8 * n * R + 16 * R + 8}
+
+    # the same FP32 solve with the test matrix regenerated at each use instead of stored
+    # (Remark 5.2): the iterates are unchanged, the handle holds n R floats less
+    bytes_stored = solve.device_bytes
+    flush.fill_(7)
+    torch.cuda.synchronize()
+    ms_rg, last_rg, cut_rg, lam_rg, _ = solve(32, keep=True, omega=S.SCGAL_OMEGA_REGEN)
+    extra["omega_regen"] = {"iter_per_s": T / (ms_rg / 1000.0), "ms_per_solve": ms_rg,
+                            "iter_per_s_stored": T / (sum(times) / len(times) / 1000.0),
+                            "device_bytes": solve.device_bytes, "device_bytes_stored": bytes_stored,
+                            "objective_equal": last_rg["p"] == last["p"], "best_cut": cut_rg,
+                            "best_cut_stored": cut, "lambda_top": float(lam_rg[0]), "lambda_top_stored": float(lam[0])}
 
     # dominant kernel: the D-matvec step, timed with CUDA events on its stream
     h = S.scgal_create_maxcut(d_rp, d_col, d_w, n, nnz, 0.0, params(32))

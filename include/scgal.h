@@ -52,6 +52,13 @@ enum { SCGAL_LMO_EQ = 0,   /* X in alpha * Delta_n: tr X = alpha (Alg. 6.1) */
        SCGAL_LMO_LEQ = 1,  /* tr X <= alpha: H = 0 when xi >= 0 (App. D.2 item 1) */
        SCGAL_LMO_DEFAULT = -1 };
 
+enum { SCGAL_OMEGA_STORED = 0,  /* Omega drawn once (FP64 normals) and kept on the device */
+       SCGAL_OMEGA_REGEN = 1 };  /* Omega never stored: each use (the Ritz step's v* Omega and
+                                    the reconstruction) regenerates its rows from the same
+                                    counter-based stream, in the solve's precision (Remark 5.2:
+                                    the sketch state halves).  FP64 solves give results
+                                    identical to STORED; FP32 ones differ by rounding. */
+
 /* Solver parameters (Alg. 6.1 inputs R, T, beta0, K and the options of Section 7.1.2). */
 typedef struct {
     int32_t  R;             /* sketch size, 1 <= R <= 32 (default 10) */
@@ -72,6 +79,8 @@ typedef struct {
     int32_t  device;        /* CUDA device ordinal of the handle; -1 = device 0 (default -1).
                                The library sets it itself on every call, independently of
                                the caller's current device. */
+    int32_t  omega;         /* SCGAL_OMEGA_*: how the n x R test matrix of the sketch is
+                               held (default STORED) */
 } scgal_params;
 
 /* One iteration record (Alg. 6.1 step t; stopping values of Eq. E.1 for the

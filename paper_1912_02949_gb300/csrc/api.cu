@@ -142,7 +142,7 @@ int setup_state(scgal_ctx* h) {
     ALLOC(h, p.ybuf, sizeof(V) * (size_t)p.ynplanes * h->ldb);
     ALLOC(h, p.vbuf, sizeof(V) * (size_t)n);
     V* om = nullptr;
-    ALLOC(h, om, sizeof(V) * (size_t)n * R);
+    if (!h->c.omega_regen) ALLOC(h, om, sizeof(V) * (size_t)n * R);   // else regenerated at each use
     p.Omega = om;
     ALLOC(h, p.S, sizeof(V) * (size_t)n * R);
     const int gmax = std::max(h->grid_elem, h->grid_spmv);
@@ -181,7 +181,7 @@ int setup_state(scgal_ctx* h) {
     if constexpr (!VT<V>::cplx) prepare_maxcut_shapes<V>();
     h->grid_ritz = std::min(h->grid_elem, ritz_resident<V>(p));
     p.nupd = update_grid<V>(h->grid_elem);   // blocks of every Lanczos update launch
-    launch_gen_omega<V>(p, grid_for((long long)n * R, SCGAL_BS, 8), s);
+    if (!h->c.omega_regen) launch_gen_omega<V>(p, grid_for((long long)n * R, SCGAL_BS, 8), s);
     launch_dual_start<V>(p, h->grid_elem, 0, s);
     CUDA_TRY(h, cudaGetLastError());
     CUDA_TRY(h, cudaStreamSynchronize(s));
@@ -212,6 +212,7 @@ int check_params(const scgal_params* p) {
     if (p->precision != 32 && p->precision != 64) return SCGAL_EINVAL;
     if (!(p->beta0 > 0.0)) return SCGAL_EINVAL;
     if (p->check_every < 1) return SCGAL_EINVAL;
+    if (p->omega != SCGAL_OMEGA_STORED && p->omega != SCGAL_OMEGA_REGEN) return SCGAL_EINVAL;
     if (p->device >= 0) {
         int count = 0;
         if (cudaGetDeviceCount(&count) != cudaSuccess || p->device >= count) {
@@ -230,6 +231,7 @@ void fill_solver_consts(scgal_ctx* h) {
     c.tol = h->prm.tol;
     c.seed = h->prm.seed;
     c.instance = h->prm.instance;
+    c.omega_regen = h->prm.omega == SCGAL_OMEGA_REGEN ? 1 : 0;
     c.R = h->R;
 }
 
@@ -563,7 +565,19 @@ int do_reconstruct(scgal_ctx* h, double* U, double* lambda, double* err, int64_t
     DevScalars sc;
     int rc = read_scalars<V>(h, &sc);
     if (rc) return rc;
-    rc = nystrom_reconstruct<V>(p.S, p.Omega, n, Rk, sc.tau, h->trace_correct, h->c.alpha, part, grid, G, L, M,
+    const V* Om = p.Omega;
+    if (h->c.omega_regen) {
+        // regenerate Omega for the reconstruction: into the Lanczos basis (per-iteration
+        // scratch) when it is large enough, else into a buffer of its own
+        V* buf = p.basis;
+        if ((size_t)(h->qmax + 1) * (size_t)h->ldb < (size_t)n * Rk) {
+            if (!h->rec_om) ALLOC(h, h->rec_om, sizeof(V) * (size_t)n * Rk);
+            buf = reinterpret_cast<V*>(h->rec_om);
+        }
+        launch_regen_omega<V>(p, buf, s);
+        Om = buf;
+    }
+    rc = nystrom_reconstruct<V>(p.S, Om, n, Rk, sc.tau, h->trace_correct, h->c.alpha, part, grid, G, L, M,
                                 scal, reinterpret_cast<D*>(h->rec_Y), reinterpret_cast<D*>(h->rec_U), lam, er, s);
     if (rc) return set_err(h, rc, rc == SCGAL_ENUMERIC ? "Nystrom factorisation failed at every shift" : "CUDA error");
     std::vector<double> hl(2 * SCGAL_RMAX);

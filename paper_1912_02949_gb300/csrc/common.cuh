@@ -149,6 +149,48 @@ template <> __device__ __forceinline__ double2 vzero<double2>() { return make_do
 __device__ __forceinline__ void from_f64(float& o, double a) { o = (float)a; }
 __device__ __forceinline__ void from_f64(double& o, double a) { o = a; }
 
+// Row `row` of the test matrix Omega (n x R, row-major) drawn afresh: entry
+// (i, c) is normal i R + c of the Omega stream, or, for complex entries, both
+// normals of pair i R + c (the layout k_gen_omega stores).  Evaluated in the
+// precision of V: bit-identical to the stored entries in FP64, within a few
+// ulps of them in FP32.  This is the storage-free test matrix of Remark 5.2
+// (Omega is never stored; every use regenerates its rows).  Entries c >= R are left unset.
+template <int RT, typename V>
+__device__ __forceinline__ void omega_row(unsigned long long seed, unsigned inst, long long row, int R,
+                                          V (&w)[RT]) {
+    typedef typename VT<V>::R Rt;
+    const long long e0 = row * R;
+    if constexpr (VT<V>::cplx) {
+#pragma unroll
+        for (int c = 0; c < RT; ++c)
+            if (c < R) {
+                Rt a, b;
+                normal_pair(seed, PURPOSE_OMEGA, 0u, inst, (unsigned)(e0 + c), a, b);
+                w[c].x = a;
+                w[c].y = b;
+            }
+    } else if ((R & 1) == 0) {   // the row starts a pair: one draw per two entries
+        static_assert(RT % 2 == 0, "even row bucket");
+#pragma unroll
+        for (int c = 0; c < RT; c += 2)
+            if (c < R) {
+                Rt a, b;
+                normal_pair(seed, PURPOSE_OMEGA, 0u, inst, (unsigned)((e0 >> 1) + (c >> 1)), a, b);
+                w[c] = a;
+                w[c + 1] = b;
+            }
+    } else {
+#pragma unroll
+        for (int c = 0; c < RT; ++c)
+            if (c < R) {
+                Rt a, b;
+                const long long e = e0 + c;
+                normal_pair(seed, PURPOSE_OMEGA, 0u, inst, (unsigned)(e >> 1), a, b);
+                w[c] = (e & 1) ? b : a;
+            }
+    }
+}
+
 // --------------------------------------------------------------------------
 // Deterministic grid reduction of NV doubles (blockDim.x == SCGAL_BS; 1-D or
 // 2-D grids, blocks numbered blockIdx.y * gridDim.x + blockIdx.x).

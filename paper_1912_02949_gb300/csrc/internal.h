@@ -56,6 +56,7 @@ struct Consts {
     double obj_factor, z_factor, normb_orig, normA_s;
     unsigned long long seed;
     unsigned instance;
+    int omega_regen;    // 1: Omega is not stored (omega_row regenerates its rows)
     int hist_cap;
     int qmax;           // Lanczos basis capacity (steps)
 };
@@ -89,7 +90,7 @@ struct KP {
     long long ldb;
     V* ybuf;            // D x of the current Lanczos step (ynplanes partial planes, stride ldb)
     V* vbuf;            // unnormalised Ritz vector
-    const V* Omega;     // n x R row-major
+    const V* Omega;     // n x R row-major (null when c.omega_regen)
     V* S;               // n x R row-major
     // reductions and scalars
     double* partials;
@@ -178,6 +179,7 @@ struct scgal_ctx {
     void* rec_U = nullptr;
     double* rec_small = nullptr;
     void* rec_cut = nullptr;
+    void* rec_om = nullptr;     // regenerated Omega, when the Lanczos basis is too small to hold it
     void* aux = nullptr;        // scratch of the single-primitive entry points
     // phase retrieval
     void* phase_extra = nullptr;
@@ -195,6 +197,7 @@ template <typename V> void launch_lanczos_update(const KP<V>& p, int grid, int i
 template <typename V> void launch_tridiag(const KP<V>& p, int q, cudaStream_t s);
 template <typename V> void launch_ritz(const KP<V>& p, int grid, cudaStream_t s);
 template <typename V> void launch_gen_omega(const KP<V>& p, int grid, cudaStream_t s);
+template <typename V> void launch_regen_omega(const KP<V>& p, V* out, cudaStream_t s);
 template <typename V> void launch_start_only(const KP<V>& p, int grid, long long t, cudaStream_t s);
 // launch-shape queries (call before any stream capture)
 template <typename V> int ritz_resident(const KP<V>& p);

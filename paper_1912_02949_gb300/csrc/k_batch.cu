@@ -1169,9 +1169,11 @@ __global__ void k_batch_fill(const int* __restrict__ row_ptr, const int* __restr
     cds[pos] = (row < n) ? cdiag[row] : 0.f;
 }
 
+// Instances that regenerate Omega run on their own graphs (k_ritz regenerates
+// the rows there); the batched kernels read a stored Omega.
 bool batch_eligible(const scgal_ctx* h) {
     return h->kind == KIND_MAXCUT && h->prec == 32 && h->n <= BATCH_NMAX && h->R <= BATCH_RMAX &&
-           h->qmax <= BATCH_QMAX;
+           h->qmax <= BATCH_QMAX && !h->c.omega_regen;
 }
 
 size_t batch_slot_bytes() { return sizeof(BatchSlot); }

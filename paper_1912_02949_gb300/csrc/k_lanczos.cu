@@ -187,11 +187,19 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ritz(KP<V> p) {
     Rt* __restrict__ vb = reinterpret_cast<Rt*>(p.vbuf);
     auto omega_acc = [&](int e, V v) {
         acc[0] += abs2(v);
-        const V* __restrict__ om = p.Omega + (size_t)e * R;
+        V orow[RT];
+        if (p.c.omega_regen) {
+            omega_row<RT>(p.c.seed, p.c.instance, e, R, orow);
+        } else {
+            const V* __restrict__ om = p.Omega + (size_t)e * R;
+#pragma unroll
+            for (int c = 0; c < RT; ++c)
+                if (c < R) orow[c] = om[c];
+        }
 #pragma unroll
         for (int c = 0; c < RT; ++c) {
             if (c < R) {
-                const V w = om[c];
+                const V w = orow[c];
                 if constexpr (CXV) {
                     acc[1 + 2 * c] += v.x * w.x + v.y * w.y;   // Re(conj(v) w)
                     acc[2 + 2 * c] += v.x * w.y - v.y * w.x;   // Im(conj(v) w)
@@ -284,6 +292,20 @@ __global__ void __launch_bounds__(SCGAL_BS) k_gen_omega(KP<V> p) {
             Om[2 * pr] = (Rt)n0;
             if (2 * pr + 1 < total) Om[2 * pr + 1] = (Rt)n1;
         }
+    }
+}
+
+// Omega regenerated for the reconstruction of a solve that does not store it
+// (the rows omega_row gives the Ritz step), one row per thread.
+template <typename V, int RT>
+__global__ void __launch_bounds__(SCGAL_BS) k_regen_omega(KP<V> p, V* out) {
+    const int n = p.c.n, R = p.c.R;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        V w[RT];
+        omega_row<RT>(p.c.seed, p.c.instance, i, R, w);
+#pragma unroll
+        for (int c = 0; c < RT; ++c)
+            if (c < R) out[(size_t)i * R + c] = w[c];
     }
 }
 
@@ -381,6 +403,13 @@ template <typename V> void launch_ritz(const KP<V>& p, int grid, cudaStream_t s)
 template <typename V> void launch_gen_omega(const KP<V>& p, int grid, cudaStream_t s) {
     k_gen_omega<V><<<grid, SCGAL_BS, 0, s>>>(p);
 }
+template <typename V> void launch_regen_omega(const KP<V>& p, V* out, cudaStream_t s) {
+    const int grid = (int)std::min<long long>(((long long)p.c.n + SCGAL_BS - 1) / SCGAL_BS, 4096);
+    if (p.c.R <= 4) k_regen_omega<V, 4><<<grid, SCGAL_BS, 0, s>>>(p, out);
+    else if (p.c.R <= 8) k_regen_omega<V, 8><<<grid, SCGAL_BS, 0, s>>>(p, out);
+    else if (p.c.R <= 16) k_regen_omega<V, 16><<<grid, SCGAL_BS, 0, s>>>(p, out);
+    else k_regen_omega<V, 32><<<grid, SCGAL_BS, 0, s>>>(p, out);
+}
 
 #define INST(V)                                                                  \
     template void launch_dual_start<V>(const KP<V>&, int, int, cudaStream_t);     \
@@ -388,6 +417,7 @@ template <typename V> void launch_gen_omega(const KP<V>& p, int grid, cudaStream
     template void launch_tridiag<V>(const KP<V>&, int, cudaStream_t);             \
     template void launch_ritz<V>(const KP<V>&, int, cudaStream_t);                \
     template void launch_gen_omega<V>(const KP<V>&, int, cudaStream_t);             \
+    template void launch_regen_omega<V>(const KP<V>&, V*, cudaStream_t);             \
     template void launch_start_only<V>(const KP<V>&, int, long long, cudaStream_t);  \
     template int ritz_resident<V>(const KP<V>&);                                      \
     template int update_grid<V>(int);                                                  \

@@ -67,7 +67,7 @@ size_t estimate_footprint(int n, long long nnz, const scgal_params& p) {
     double bytes = 4.0 * (n + 1) + 4.0 * nnz + vb * nnz          // CSR (values only for general weights)
                    + vb * (qmax + 1) * ldb                       // Lanczos basis
                    + vb * 4.0 * n                                // Y, v, cdiag, dvec
-                   + 2.0 * vb * n * p.R                          // Omega, S
+                   + (p.omega == SCGAL_OMEGA_REGEN ? 1.0 : 2.0) * vb * n * p.R   // S, and Omega unless regenerated
                    + 16.0 * n                                    // z, y
                    + 2.0 * 16.0 * n * p.R                        // reconstruction Y, U (FP64)
                    + 60.0 * p.T_max + 8.0 * 65 * 1216 + 65536    // history, q table, partials, scalars
