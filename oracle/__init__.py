@@ -19,7 +19,9 @@ Modules (each function cites the passage it follows):
 * ``nystrom``     -- NystromSketch, Alg. 5.1 / Alg. B.1, trace correction (App. B.4).
 * ``sketchycgal`` -- SketchyCGAL, Alg. 6.1, with the dual step of Eq. 6.4, the
                      objective tracking of Section 6.2.2, the stopping rule
-                     Eq. E.1 and the trace-bounded LMO of App. D.2.
+                     Eq. E.1 and the trace-bounded LMO of App. D.2; and the
+                     general template of Alg. D.1 with inequality constraints
+                     A(X) <= b (App. D.3), pinned by ``tests/test_oracle_general.py``.
 * ``cgal_dense``  -- CGAL with an explicit matrix iterate, Alg. 3.1 (tiny n only).
 * ``rounding``    -- MaxCut rounding (Section 7.2.1), brute-force max cut,
                      phase-retrieval rounding and error (Section 7.3.2-7.3.3).

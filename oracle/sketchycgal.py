@@ -28,6 +28,23 @@ Readings (where the paper is silent or ambiguous):
 * Trace-bounded LMO (App. D.2 item 1): if xi >= 0 the direction is H = 0, so
   z, S, tau, p are all scaled by (1 - eta).
 * gamma = beta0 when z = b exactly.
+
+General template (App. D, Alg. D.1) with the inclusion A(X) in K instead of
+A(X) = b, for K = {b} ("eq", the model problem) or K = {u : u <= b} ("leq",
+inequality constraints, App. D.3 item 1), through the slack w in K:
+    w = proj_K(z + y / beta)                       gradient weights y + beta (z - w)
+    wbar = proj_K(z_new + y / beta_+), beta_+ = beta0 sqrt(t+2)
+    y <- y + gamma (z_new - wbar),  gamma ||z_new - wbar||^2 <= beta eta^2 alpha^2 ||A||^2
+(the last bound equals the one of Eq. 6.4).  Readings:
+* proj onto {u <= b} is the componentwise min(w, b), i.e. b + (w - b)_-; the
+  paper prints (w - b)_-, which is that projection less b.
+* The paper states no stopping rule for the template.  The bound of Eq. 6.6
+  repeated with the slack (convexity of the augmented Lagrangian in X, and
+  L(X*) <= p* at w = A X* for a feasible X*) gives
+      p - p* <= p + <y, w> + beta/2 <z - w, z + w> - alpha xi,
+  which is Eq. E.1's numerator with b replaced by w = proj_K(z + y / beta);
+  the infeasibility is the distance to K, ||z - proj_K(z)|| / (1 + ||b||).
+  For K = {b} both are exactly Eq. E.1.
 """
 from __future__ import annotations
 
@@ -65,22 +82,44 @@ def dual_step(normsq_zb: float, t: int, alpha: float, beta0: float, normA: float
     return min(beta0, 4.0 * alpha * alpha * beta0 * normA * normA / ((t + 1) ** 1.5 * normsq_zb))
 
 
-def stopping_values(prob, p, y, z, beta, xi, lmo):
-    """Relative gap and infeasibility of Eq. E.1 in the original units."""
+def proj_K(u, b, kset: str):
+    """Euclidean projection onto K (App. D.3): K = {b}, or K = {u <= b}."""
+    if kset == "eq":
+        return b
+    if kset == "leq":
+        return np.minimum(u, b)
+    raise ValueError(kset)
+
+
+def al_weights(z, y, beta, b, kset: str):
+    """Weights u = y + beta (z - w) of D = C + A*(u) (Alg. D.1), with the slack
+    w = proj_K(z + y / beta); for K = {b}, w = b (Eq. 6.1)."""
+    if kset == "eq":
+        return y + beta * (z - b)
+    return y + beta * (z - proj_K(z + y / beta, b, kset))
+
+
+def stopping_values(prob, p, y, z, beta, xi, lmo, kset: str = "eq"):
+    """Relative gap and infeasibility of Eq. E.1 in the original units (for
+    K = {u <= b}: b replaced by the slack w = proj_K(z + y / beta) in the gap,
+    and the infeasibility measured as the distance of z to K)."""
     b = prob.b
+    w = b if kset == "eq" else proj_K(z + y / beta, b, kset)
     lam_term = prob.alpha * (min(0.0, xi) if lmo == "leq" else xi)
-    num = p + float(np.dot(y, b)) + 0.5 * beta * float(np.dot(z - b, z + b)) - lam_term
+    num = p + float(np.dot(y, w)) + 0.5 * beta * float(np.dot(z - w, z + w)) - lam_term
     p_orig = prob.obj_factor * p
     relgap = prob.obj_factor * num / (1.0 + abs(p_orig))
-    infeas = prob.z_factor * float(np.linalg.norm(z - b)) / (1.0 + float(np.linalg.norm(prob.b_orig)))
+    dz = z - proj_K(z, b, kset)
+    infeas = prob.z_factor * float(np.linalg.norm(dz)) / (1.0 + float(np.linalg.norm(prob.b_orig)))
     return relgap, infeas, p_orig
 
 
 def sketchy_cgal(prob, R: int, T: int, seed: int = 0, instance: int = 0, beta0: float = 1.0,
                  K: float = math.inf, lmo: str | None = None, trace_correct: bool | None = None,
                  tol: float | None = None, store_basis: bool = True,
-                 record_v: bool = False, t_start: int = 1) -> SolveResult:
-    """Run Alg. 6.1 for t = t_start .. T (t_start > 1 only for timing samples)."""
+                 record_v: bool = False, t_start: int = 1, kset: str = "eq") -> SolveResult:
+    """Run Alg. 6.1 for t = t_start .. T (t_start > 1 only for timing samples);
+    kset = "leq" runs Alg. D.1 with K = {u : u <= b}."""
     n, d = prob.n, prob.d
     cplx = prob.complex_
     if lmo is None:
@@ -100,7 +139,7 @@ def sketchy_cgal(prob, R: int, T: int, seed: int = 0, instance: int = 0, beta0: 
     for t in range(t_start, T + 1):
         beta = beta0 * math.sqrt(t + 1)
         eta = 2.0 / (t + 1)
-        w = y + beta * (z - prob.b)
+        w = al_weights(z, y, beta, prob.b, kset)
 
         def Mv(u, w=w):
             return prob.C_apply(u) + prob.Astar_apply(w, u)
@@ -109,7 +148,7 @@ def sketchy_cgal(prob, R: int, T: int, seed: int = 0, instance: int = 0, beta0: 
         v1 = gaussian_vector(seed, PURPOSE_LANCZOS, t, instance, n, cplx)
         xi, v, info = approx_min_evec(Mv, v1, q, store_basis)
         v = v / np.linalg.norm(v)
-        relgap, infeas, p_orig = stopping_values(prob, p, y, z, beta, xi, lmo)
+        relgap, infeas, p_orig = stopping_values(prob, p, y, z, beta, xi, lmo, kset)
         rec = dict(t=t, q=q, k=info["k"], xi=xi, p=p, p_orig=p_orig, relgap=relgap, infeas=infeas)
         if tol is not None and relgap <= tol and infeas <= tol:
             rec["gamma"] = 0.0
@@ -128,7 +167,10 @@ def sketchy_cgal(prob, R: int, T: int, seed: int = 0, instance: int = 0, beta0: 
             p = (1.0 - eta) * p + eta * alpha * vCv
             sketch.rank_one_update(math.sqrt(alpha) * v, eta)
             h_taken = True
-        zb = z - prob.b
+        if kset == "eq":
+            zb = z - prob.b
+        else:
+            zb = z - proj_K(z + y / (beta0 * math.sqrt(t + 2)), prob.b, kset)
         nzb2 = float(np.dot(zb, zb))
         gamma = dual_step(nzb2, t, alpha, beta0, prob.normA_s)
         y_new = y + gamma * zb
