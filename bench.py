@@ -484,17 +484,18 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def params(prec, tol=0.0, omega=0):
+    def params(prec, tol=0.0, omega=0, kset=0):
         return S.scgal_params_default(R=R, T_max=T, precision=prec, seed=replica_seed(rank), tol=tol, device=local,
-                                      omega=omega)
+                                      omega=omega, kset=kset,
+                                      lmo=S.SCGAL_LMO_LEQ if kset == S.SCGAL_K_LEQ else S.SCGAL_LMO_DEFAULT)
 
-    def solve(prec, host=False, tol=0.0, keep=False, omega=0):
+    def solve(prec, host=False, tol=0.0, keep=False, omega=0, kset=0):
         """One full solve; returns (ms, last record, best cut, lambda, handle or None)."""
         bufs = (rp_h, col_h, w_h, U_h) if host else (d_rp, d_col, d_w, U_dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h = S.scgal_create_maxcut(bufs[0], bufs[1], bufs[2], n, nnz, 0.0, params(prec, tol, omega))
+        h = S.scgal_create_maxcut(bufs[0], bufs[1], bufs[2], n, nnz, 0.0, params(prec, tol, omega, kset))
         S.scgal_set_stream(h, stream.cuda_stream)
         if keep:
             solve.device_bytes = S.scgal_get_info(h)["device_bytes"]
@@ -561,6 +562,17 @@ def main():
                             "device_bytes": solve.device_bytes, "device_bytes_stored": bytes_stored,
                             "objective_equal": last_rg["p"] == last["p"], "best_cut": cut_rg,
                             "best_cut_stored": cut, "lambda_top": float(lam_rg[0]), "lambda_top_stored": float(lam[0])}
+
+    # the general template (Alg. D.1) on the same graph: diag X <= 1, tr X <= n
+    # (K = {u <= b}); the projection is fused into the dual and z-update kernels
+    flush.fill_(9)
+    torch.cuda.synchronize()
+    ms_k, last_k, cut_k, lam_k, _ = solve(32, kset=S.SCGAL_K_LEQ)
+    extra["inequality_leq"] = {"iter_per_s": T / (ms_k / 1000.0), "ms_per_solve": ms_k,
+                               "objective_T": last_k["p"], "relgap_T": last_k["relgap"], "infeas_T": last_k["infeas"],
+                               "best_cut": cut_k, "objective_T_equality": last["p"],
+                               "desc": "MaxCut SDP with diag X <= 1 and tr X <= n (general template, "
+                                       "K = {u <= 1}), same graph, R, T, FP32 path"}
 
     # dominant kernel: the D-matvec step, timed with CUDA events on its stream
     h = S.scgal_create_maxcut(d_rp, d_col, d_w, n, nnz, 0.0, params(32))

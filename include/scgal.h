@@ -59,6 +59,15 @@ enum { SCGAL_OMEGA_STORED = 0,  /* Omega drawn once (FP64 normals) and kept on t
                                     the sketch state halves).  FP64 solves give results
                                     identical to STORED; FP32 ones differ by rounding. */
 
+enum { SCGAL_K_EQ = 0,    /* A(X) = b: the model problem (Eq. 2.2, Alg. 6.1) */
+       SCGAL_K_LEQ = 1 };  /* A(X) <= b componentwise: the general template of App. D with
+                              K = {u : u <= b} (App. D.3 item 1), through the slack
+                              w = proj_K(z + y / beta) = min(z + y / beta, b) in the gradient
+                              weights y + beta (z - w) and in the dual step (Alg. D.1).  The
+                              stopping rule uses w in place of b in Eq. E.1's numerator and
+                              the distance ||(z - b)_+|| to K as the infeasibility.  For
+                              MaxCut, b = 1: diag X <= 1. */
+
 /* Solver parameters (Alg. 6.1 inputs R, T, beta0, K and the options of Section 7.1.2). */
 typedef struct {
     int32_t  R;             /* sketch size, 1 <= R <= 32 (default 10) */
@@ -81,6 +90,7 @@ typedef struct {
                                the caller's current device. */
     int32_t  omega;         /* SCGAL_OMEGA_*: how the n x R test matrix of the sketch is
                                held (default STORED) */
+    int32_t  kset;          /* SCGAL_K_*: the constraint set K of A(X) in K (default EQ) */
 } scgal_params;
 
 /* One iteration record (Alg. 6.1 step t; stopping values of Eq. E.1 for the

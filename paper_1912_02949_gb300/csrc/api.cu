@@ -213,6 +213,7 @@ int check_params(const scgal_params* p) {
     if (!(p->beta0 > 0.0)) return SCGAL_EINVAL;
     if (p->check_every < 1) return SCGAL_EINVAL;
     if (p->omega != SCGAL_OMEGA_STORED && p->omega != SCGAL_OMEGA_REGEN) return SCGAL_EINVAL;
+    if (p->kset != SCGAL_K_EQ && p->kset != SCGAL_K_LEQ) return SCGAL_EINVAL;
     if (p->device >= 0) {
         int count = 0;
         if (cudaGetDeviceCount(&count) != cudaSuccess || p->device >= count) {
@@ -232,6 +233,7 @@ void fill_solver_consts(scgal_ctx* h) {
     c.seed = h->prm.seed;
     c.instance = h->prm.instance;
     c.omega_regen = h->prm.omega == SCGAL_OMEGA_REGEN ? 1 : 0;
+    c.kleq = h->prm.kset == SCGAL_K_LEQ ? 1 : 0;
     c.R = h->R;
 }
 

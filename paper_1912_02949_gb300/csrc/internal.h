@@ -33,8 +33,9 @@ struct DevScalars {
     double nv2;         // ||v||^2 of the unnormalised Ritz vector
     double vCv;         // v* C v (unnormalised v)
     double p, tau;      // <C', X'>, tr X' (scaled)
-    double yb, zbzpb, nzb2;   // <y,b>, <z-b, z+b>, ||z-b||^2 of the state before the update
-    double nzb2_new, yzb_new, yy; // after the z update: ||z-b||^2, <y, z-b>, ||y||^2
+    double yb, zbzpb, nzb2;   // <y,w>, <z-w, z+w>, ||z - proj_K(z)||^2 of the state before the
+                              // update, w = proj_K(z + y / beta) (w = b for K = {b})
+    double nzb2_new, yzb_new, yy; // after the z update: ||z-wbar||^2, <y, z-wbar>, ||y||^2
     double gamma;
     double r[2 * SCGAL_RMAX];   // Omega* v (re, im) of the unnormalised Ritz vector
 };
@@ -57,6 +58,7 @@ struct Consts {
     unsigned long long seed;
     unsigned instance;
     int omega_regen;    // 1: Omega is not stored (omega_row regenerates its rows)
+    int kleq;           // 1: K = {u <= b} (slack w = min(z + y / beta, b)); 0: K = {b}
     int hist_cap;
     int qmax;           // Lanczos basis capacity (steps)
 };

@@ -1170,10 +1170,11 @@ __global__ void k_batch_fill(const int* __restrict__ row_ptr, const int* __restr
 }
 
 // Instances that regenerate Omega run on their own graphs (k_ritz regenerates
-// the rows there); the batched kernels read a stored Omega.
+// the rows there); the batched kernels read a stored Omega.  Likewise for
+// K = {u <= b}: the batched kernels implement K = {b}.
 bool batch_eligible(const scgal_ctx* h) {
     return h->kind == KIND_MAXCUT && h->prec == 32 && h->n <= BATCH_NMAX && h->R <= BATCH_RMAX &&
-           h->qmax <= BATCH_QMAX && !h->c.omega_regen;
+           h->qmax <= BATCH_QMAX && !h->c.omega_regen && !h->c.kleq;
 }
 
 size_t batch_slot_bytes() { return sizeof(BatchSlot); }

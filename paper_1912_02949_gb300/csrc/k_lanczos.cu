@@ -23,7 +23,10 @@ namespace scgal {
 // Dual step of iteration t (Eq. 6.3, gamma from the previous kernel), then the
 // set-up of iteration t+1: beta, eta, the diagonal of D (MaxCut) or the weights
 // w (phase retrieval), the stopping scalars <y,b>, <z-b,z+b>, ||z-b||^2 of the
-// new state, and the random Lanczos start W_0 with its squared norm.
+// new state, and the random Lanczos start W_0 with its squared norm.  With
+// K = {u <= b} (Alg. D.1) b is replaced by the slack: wbar = min(z + y_old /
+// beta_{t+1}, b) in the dual step, w = min(z + y_new / beta_{t+1}, b) in the
+// weights and the gap sums, and the infeasibility sum is ||(z - b)_+||^2.
 template <typename V>
 __global__ void __launch_bounds__(SCGAL_BS) k_dual_start(KP<V> p, int do_dual) {
     typedef typename VT<V>::R Rt;
@@ -40,15 +43,18 @@ __global__ void __launch_bounds__(SCGAL_BS) k_dual_start(KP<V> p, int do_dual) {
     for (int i = gt; i < d; i += st) {
         const double bi = p.c.b_const ? p.c.bconst : p.b[i];
         const double zi = p.z[i];
-        const double zb = zi - bi;
         double yi = p.y[i];
         if (do_dual) {
-            yi = fma(gamma, zb, yi);
+            const double wb = p.c.kleq ? fmin(zi + yi / beta1, bi) : bi;
+            yi = fma(gamma, zi - wb, yi);
             p.y[i] = yi;
         }
-        a_yb = fma(yi, bi, a_yb);
-        a_zz = fma(zb, zi + bi, a_zz);
-        a_nzb = fma(zb, zb, a_nzb);
+        const double wk = p.c.kleq ? fmin(zi + yi / beta1, bi) : bi;   // slack of iteration t+1
+        const double zb = zi - wk;
+        a_yb = fma(yi, wk, a_yb);
+        a_zz = fma(zb, zi + wk, a_zz);
+        const double zk = p.c.kleq ? fmax(zi - bi, 0.0) : zb;           // z - proj_K(z)
+        a_nzb = fma(zk, zk, a_nzb);
         const double wi = p.c.sA * fma(beta1, zb, yi);
         if (p.c.kind == KIND_MAXCUT)
             p.dvec[i] = (Rt)((double)p.cdiag[i] + wi);

@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(SCGAL_BS) k_spmv_step(KP<V> p, int i) {
 // After the Ritz vector: v* C v (primitive (1), one more CSR pass), the primal
 // updates of Eq. 6.2 z <- (1-eta) z + eta A(alpha v v*), S <- (1-eta) S +
 // eta alpha v (v* Omega) with v = vbuf / ||vbuf||, the objective and trace
-// updates (Section 6.2.2, Eq. B.2), and the dual step size of Eq. 6.4.
+// updates (Section 6.2.2, Eq. B.2), and the dual step size of Eq. 6.4 (with
+// z - wbar, wbar = min(z + y / beta_{t+1}, b), for K = {u <= b}: Alg. D.1).
 template <typename V, int WK>
 __global__ void __launch_bounds__(SCGAL_BS) k_vcv_update(KP<V> p) {
     DevScalars* sc = p.sc;
@@ -148,12 +149,14 @@ __global__ void __launch_bounds__(SCGAL_BS) k_vcv_update(KP<V> p) {
     if (threadIdx.x < R) rr[threadIdx.x] = (V)sc->r[2 * threadIdx.x];
     __syncthreads();
     double a_nzb = 0.0, a_yzb = 0.0, a_yy = 0.0;
+    const double betap = p.c.beta0 * sqrt((double)(sc->t + 2));   // beta_{t+1}: wbar of Alg. D.1
     const int gt = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
     for (int e = gt; e < n; e += st) {
         const double ve = (double)v[e];
         const double zi = fma(1.0 - eta, p.z[e], zc * ve * ve);
         p.z[e] = zi;
-        const double zb = zi - (p.c.b_const ? p.c.bconst : p.b[e]);
+        const double bi = p.c.b_const ? p.c.bconst : p.b[e];
+        const double zb = zi - (p.c.kleq ? fmin(zi + p.y[e] / betap, bi) : bi);
         a_nzb = fma(zb, zb, a_nzb);
         if (p.c.K_finite) {
             const double yi = p.y[e];

@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ph_p2(KP<V> p, const typename VT<V
         const int take = sc->take_h;
         const double zc = take ? eta * p.c.alpha * p.c.sA / nv2 : 0.0;
         double a_nzb = 0.0, a_yzb = 0.0, a_yy = 0.0;
+        const double betap = p.c.beta0 * sqrt((double)(sc->t + 2));   // beta_{t+1}: wbar of Alg. D.1
         const size_t base = (size_t)j * n + (size_t)l2base * n1;
         for (int idx = threadIdx.x; idx < RPB * n1; idx += blockDim.x) {
             const size_t i = base + idx;
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ph_p2(KP<V> p, const typename VT<V
             const double a2 = (double)X.x * X.x + (double)X.y * X.y;
             const double zi = fma(1.0 - eta, p.z[i], zc * a2);
             p.z[i] = zi;
-            const double zb = zi - p.b[i];
+            const double zb = zi - (p.c.kleq ? fmin(zi + p.y[i] / betap, p.b[i]) : p.b[i]);
             a_nzb = fma(zb, zb, a_nzb);
             if (p.c.K_finite) {
                 const double yi = p.y[i];

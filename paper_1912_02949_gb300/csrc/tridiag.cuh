@@ -228,7 +228,8 @@ __device__ void tridiag_body(const KP<V>& p, int q, double* smt) {
     }
     if (threadIdx.x == 0) {
         if (k == 1) xi = a[0] * scale;
-        // stopping rule of Eq. E.1 on the state of iteration t (before its update)
+        // stopping rule of Eq. E.1 on the state of iteration t (before its update);
+        // for K = {u <= b} the sums hold <y,w>, <z-w,z+w> and ||(z-b)_+||^2 (Alg. D.1)
         const Consts& c = p.c;
         const double lam = c.alpha * ((c.lmo == SCGAL_LMO_LEQ) ? fmin(0.0, xi) : xi);
         const double num = sc->p + sc->yb + 0.5 * sc->beta * sc->zbzpb - lam;

@@ -26,6 +26,7 @@ SCGAL_EBUSY = -6
 SCGAL_ESTATE = -7
 SCGAL_LMO_EQ, SCGAL_LMO_LEQ, SCGAL_LMO_DEFAULT = 0, 1, -1
 SCGAL_OMEGA_STORED, SCGAL_OMEGA_REGEN = 0, 1
+SCGAL_K_EQ, SCGAL_K_LEQ = 0, 1
 
 
 class ScgalError(RuntimeError):
@@ -38,7 +39,7 @@ class scgal_params(Structure):
     _fields_ = [("R", c_int32), ("T_max", c_int32), ("tol", c_double), ("beta0", c_double), ("K", c_double),
                 ("lmo", c_int32), ("scale", c_int32), ("trace_correct", c_int32), ("precision", c_int32),
                 ("seed", c_uint64), ("instance", c_uint32), ("check_every", c_int32), ("device", c_int32),
-                ("omega", c_int32)]
+                ("omega", c_int32), ("kset", c_int32)]
 
 
 class scgal_stats(Structure):

@@ -84,6 +84,10 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert S.scgal_params_default().omega == S.SCGAL_OMEGA_STORED
     ok = S.scgal_params_default(R=2, omega=2)
     assert lib.scgal_create_maxcut(rp, cl, None, 2, 2, 0.0, ctypes.byref(ok), ctypes.byref(h)) == S.SCGAL_EINVAL
+    # and an unknown constraint set
+    assert S.scgal_params_default().kset == S.SCGAL_K_EQ
+    ok = S.scgal_params_default(R=2, kset=2)
+    assert lib.scgal_create_maxcut(rp, cl, None, 2, 2, 0.0, ctypes.byref(ok), ctypes.byref(h)) == S.SCGAL_EINVAL
     m = (ctypes.c_double * 64)()
     big = S.scgal_params_default(R=17)
     assert lib.scgal_create_phase(m, 1, 16, m, 0.0, ctypes.byref(big), ctypes.byref(h)) == S.SCGAL_EINVAL
