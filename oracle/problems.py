@@ -132,3 +132,88 @@ class PhaseProblem:
 
     def dense_C(self):
         return self.sC * np.eye(self.n, dtype=np.complex128)
+
+
+def window_overlaps(N: int, M: int, s: int) -> np.ndarray:
+    """ov[k] = |[0, M) intersect ([k s, k s + M) mod N)|, k = 0 .. N/s - 1 (one dimension)."""
+    K = N // s
+    base = np.zeros(N, dtype=bool)
+    base[:M] = True
+    ov = np.empty(K, dtype=np.int64)
+    for k in range(K):
+        w = np.zeros(N, dtype=bool)
+        w[(k * s + np.arange(M)) % N] = True
+        ov[k] = int(np.sum(base & w))
+    return ov
+
+
+class PtychoProblem:
+    """Fourier-ptychography phase retrieval SDP (Section 7.4, App. F.2), same
+    SDP as Eq. 7.3 (C = I, tr X <= alpha) with the measurement vectors
+        a_{(j-1)m + l} = W*_m(l, :) Phi_j,
+    where chi in C^n, n = N^2, is the Fourier-domain image (row-major N x N),
+    Phi_j (m x n, one nonzero per row) selects the M x M aperture window of
+    illumination j = (kr, kc), 0 <= kr, kc < K, at offset (kr s, kc s) with
+    indices taken mod N, weighted by the pupil p (M x M, unit modulus):
+        (Phi_j u)[r M + c] = p[r M + c] u[((kr s + r) mod N) N + (kc s + c) mod N],
+    and W_m is the two-dimensional M x M DFT (m = M^2, unnormalised, row-major
+    low-resolution pixel order), W*_m its conjugate transpose (= m ifft2).
+    Primitives:
+        (1) u -> u
+        (2) (u, z) -> sum_j Phi_j^* W_m (z_j .* W*_m Phi_j u)
+        (3) u -> [ |W*_m Phi_j u|^2 ]_j
+    ||A||: with g_i = Phi_j^* W_m e_l (A_i = g_i g_i^*; |entries| = 1 on window j),
+    sum over l' of |g_{j'l'}^* g_i|^2 = ||W*_m Phi_j' g_i||^2 = m |W_j cap W_j'|.
+    On a regular periodic grid (K s = N) every row of the nonnegative Gram matrix
+    G_ik = |g_i^* g_k|^2 has the sum m (sum_k ov(k))^2, so ||A||^2 = lambda_max(G)
+    equals it (Perron-Frobenius): ||A|| = M sum_k ov(k).  ||C||_F = sqrt(n).
+    alpha defaults to 1.5 for a unit-norm signal (Section 7.4.2).
+    """
+
+    complex_ = True
+
+    def __init__(self, N: int, M: int, s: int, pupil, b, alpha: float | None = None, scale: bool = True):
+        if N % s or M > N:
+            raise ValueError("windows need s | N and M <= N")
+        self.N, self.M, self.s, self.K = int(N), int(M), int(s), int(N // s)
+        self.n = self.N * self.N
+        self.m = self.M * self.M
+        self.L_masks = self.K * self.K
+        self.d = self.L_masks * self.m
+        self.pupil = np.asarray(pupil, dtype=np.complex128).reshape(self.M, self.M)
+        self.b_orig = np.asarray(b, dtype=np.float64).reshape(-1)
+        self.normA = float(self.M * np.sum(window_overlaps(self.N, self.M, self.s)))
+        self.normC = math.sqrt(self.n)
+        self.alpha_orig = float(1.5 if alpha is None else alpha)
+        r = np.arange(self.M)
+        # pixel indices of every window: idx[j] is M x M
+        self.idx = np.empty((self.L_masks, self.M, self.M), dtype=np.int64)
+        for kr in range(self.K):
+            for kc in range(self.K):
+                rows = (kr * self.s + r) % self.N
+                cols = (kc * self.s + r) % self.N
+                self.idx[kr * self.K + kc] = rows[:, None] * self.N + cols[None, :]
+        self._set_scale(scale)
+
+    _set_scale = MaxCutProblem._set_scale
+
+    def _forward(self, u):
+        """W*_m Phi_j u for every j: L x M x M."""
+        U = self.pupil[None, :, :] * np.asarray(u)[self.idx]
+        return self.m * np.fft.ifft2(U, axes=(1, 2))
+
+    def C_apply(self, u):
+        return self.sC * u
+
+    def Astar_apply(self, z, u):
+        Z = np.asarray(z).reshape(self.L_masks, self.M, self.M)
+        back = np.fft.fft2(Z * self._forward(u), axes=(1, 2))
+        out = np.zeros(self.n, dtype=np.complex128)
+        np.add.at(out, self.idx.reshape(-1), (np.conj(self.pupil)[None, :, :] * back).reshape(-1))
+        return self.sA * out
+
+    def A_of_uu(self, u):
+        return self.sA * (np.abs(self._forward(u)) ** 2).reshape(-1)
+
+    def dense_C(self):
+        return self.sC * np.eye(self.n, dtype=np.complex128)

@@ -174,6 +174,47 @@ def phase_problem(n: int, L: int = 12, seed: int = 0) -> PhaseData:
     return PhaseData(n, L, chi, masks, b.reshape(-1).astype(np.float64))
 
 
+@dataclass
+class PtychoData:
+    N: int
+    M: int
+    s: int
+    chi: np.ndarray      # Fourier-domain image, n = N^2, unit norm
+    pupil: np.ndarray    # M x M, unit modulus
+    b: np.ndarray        # L m intensities, window-major
+
+
+def ptycho_problem(N: int = 320, M: int = 64, s: int = 20, seed: int = 0) -> PtychoData:
+    """Synthetic Fourier-ptychography data in the shape of the paper's FP study
+    (n = 320^2 image, 64^2-pixel low-resolution frames; App. F.2): a smooth
+    nonnegative N x N image (a sum of 40 Gaussian blobs with random centres,
+    widths N/40 .. N/8 and weights), chi = its unnormalised 2-D DFT scaled to
+    unit norm; a K x K grid of periodic aperture windows (K = N / s) whose
+    offsets overlap by M - s pixels; a unit-modulus defocus pupil
+    exp(i pi (rho^2 / (M/2)^2) / 2); b = |W*_m Phi_j chi|^2 window by window."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[0:N, 0:N].astype(np.float64)
+    img = np.zeros((N, N))
+    for _ in range(40):
+        cy, cx = rng.uniform(0, N, 2)
+        w = rng.uniform(N / 40.0, N / 8.0)
+        img += rng.uniform(0.2, 1.0) * np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (2 * w * w))
+    chi = np.fft.fft2(img).reshape(-1)
+    chi /= np.linalg.norm(chi)
+    r = np.arange(M) - M / 2.0
+    rho2 = r[:, None] ** 2 + r[None, :] ** 2
+    pupil = np.exp(1j * np.pi * 0.5 * rho2 / (M / 2.0) ** 2)
+    K = N // s
+    out = np.empty((K * K, M, M))
+    ar = np.arange(M)
+    X = chi.reshape(N, N)
+    for kr in range(K):
+        for kc in range(K):
+            win = X[np.ix_((kr * s + ar) % N, (kc * s + ar) % N)]
+            out[kr * K + kc] = np.abs(M * M * np.fft.ifft2(pupil * win)) ** 2
+    return PtychoData(N, M, s, chi, pupil.reshape(-1), out.reshape(-1))
+
+
 def serving_requests(count: int, rate: float, seed: int = 0, n_lo: int = 100, n_hi: int = 50000,
                      deg_lo: float = 4.0, deg_hi: float = 16.0):
     """Poisson arrivals (exponential gaps at `rate` per second); sizes
