@@ -215,6 +215,62 @@ def run_phase(S, sm_mhz: float, T: int = 1000, seed: int = SEED):
     return out
 
 
+PTYCHO_DESC = ("Fourier-ptychography phase retrieval SDP (Section 7.4 shape): n = 320^2 Fourier-domain image of a "
+               "synthetic smooth picture (unit norm), 64 x 64 aperture windows on a periodic 16 x 16 grid (step 20, "
+               "L = 256 illuminations, d = 1,048,576), unit-modulus defocus pupil; C = I, alpha = 1.5, "
+               "tr X <= alpha; R = 5")
+
+
+def ptycho_matvec_flops(N: int, M: int, s: int) -> float:
+    """Per D-matvec: two 2-D M x M FFTs per window (5 m log2 m each, m = M^2),
+    the pupil, weight and conjugate-pupil products (14 m), the per-pixel sum of
+    the L m window values (2 flops each) and sC x (2 n)."""
+    K = N // s
+    L, m, n = K * K, M * M, N * N
+    return L * (10.0 * m * math.log2(m) + 14.0 * m) + 2.0 * L * m + 2.0 * n
+
+
+def run_ptycho(S, sm_mhz: float, T: int = 1000, T64: int = 200, seed: int = SEED):
+    """The Fourier-ptychography workload through the C ABI: FP32 for T iterations
+    and FP64 for T64 (host-timed around the synchronous solve), the relative
+    error of the recovered image (top eigenvector of the reconstruction, global
+    phase removed), and the FP32 D-matvec timed with CUDA events on its stream
+    against the FP32 ALU roofline."""
+    import numpy as np
+    import workloads as W
+    N, M, s, R = 320, 64, 20, 5
+    pd = W.ptycho_problem(N, M, s, seed=seed)
+    K = N // s
+    out = {"desc": PTYCHO_DESC, "N": N, "M": M, "step": s, "L": K * K, "n": N * N, "d": K * K * M * M, "R": R,
+           "T": T, "T_fp64": T64}
+    for prec, TT in ((32, T), (64, T64)):
+        h = S.scgal_create_ptycho(pd.pupil, M, N, s, pd.b, 0.0,
+                                  S.scgal_params_default(R=R, T_max=TT, precision=prec, seed=seed))
+        if prec == 32:
+            mv_ms = S.scgal_time_kernel(h, 0, 200)
+        t0 = time.perf_counter()
+        rc, last = S.scgal_solve(h, TT)
+        sec = time.perf_counter() - t0
+        U, lam, err, _ = S.scgal_reconstruct(h, want_cut=False)
+        h.close()
+        chi = np.sqrt(max(float(lam[0]), 0.0)) * U[0]
+        ph = np.vdot(chi, pd.chi)
+        ph = ph / abs(ph) if abs(ph) > 0 else 1.0
+        image_err = float(np.linalg.norm(ph * chi - pd.chi) / np.linalg.norm(pd.chi))
+        out[f"fp{prec}"] = {"iter_per_s": TT / sec, "seconds": sec, "relgap_T": last["relgap"],
+                            "infeas_T": last["infeas"], "image_rel_error": image_err}
+    flops = ptycho_matvec_flops(N, M, s)
+    peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / (mv_ms * 1e-3) / 1e12
+    n, Lm = N * N, K * K * M * M
+    out["matvec_roofline"] = {"bound": "alu", "kernel": "ptychography D-matvec (k_fp_apply + k_fp_gather)",
+                              "ms_per_launch": mv_ms, "flops_per_launch": flops, "achieved": achieved,
+                              "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                              "bytes_per_launch": 8 * n + 4 * Lm + 8 * n,
+                              "peak_source": "152 SMs x 128 FP32 lanes x 2 x sampled clock"}
+    return out
+
+
 LARGE_DESC = ("large MaxCut SDP: 2048 x 4096 torus plus 10% long-range edges (n = 2^23), +/-1 weights, "
               "R=10, T=1000, FP32 sketch and basis on one GPU, FP64 reconstruction and integer rounding")
 
@@ -427,6 +483,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=152)
     ap.add_argument("--no-phase", action="store_true", help="skip the phase-retrieval leg")
     ap.add_argument("--no-large", action="store_true", help="skip the n = 2^23 torus MaxCut leg")
+    ap.add_argument("--no-ptycho", action="store_true", help="skip the Fourier-ptychography leg")
     ap.add_argument("--profile-serve", type=int, default=0,
                     help="only run K requests of the serving workload with T_max=300 (for profiler captures)")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
@@ -602,6 +659,10 @@ def main():
     if not args.no_phase:
         phase = run_phase(S, (clk or {}).get("sm_mhz") or 2070.0)
 
+    ptycho = None
+    if not args.no_ptycho:
+        ptycho = run_ptycho(S, (clk or {}).get("sm_mhz") or 2070.0)
+
     serving = None
     if args.serve_requests > 0:
         local, lat = run_serving(S, args.serve_requests, args.serve_slots, seed=replica_seed(rank))
@@ -625,7 +686,7 @@ def main():
                 "gpu_launches": args.steps * launches_per_solve(n, T),
                 "clocks": clk, "solve": {"relgap_T": last["relgap"], "infeas_T": last["infeas"],
                                          "objective_T": last["p"], "best_cut": cut, "lambda_top3": list(lam[:3])},
-                "kernels_ms_per_launch": kern, "kernel_share_of_solve": share, "serving": serving, "phase_retrieval": phase, "large_maxcut": large, **extra}
+                "kernels_ms_per_launch": kern, "kernel_share_of_solve": share, "serving": serving, "phase_retrieval": phase, "ptychography": ptycho, "large_maxcut": large, **extra}
         if hist32:
             hit = next((r["t"] for r in hist32 if r["relgap"] <= 1e-3 and r["infeas"] <= 1e-3), None)
             line["solve"]["first_t_gap_1e-3"] = hit

@@ -154,6 +154,27 @@ int scgal_create_maxcut(const int32_t* row_ptr, const int32_t* col, const double
 int scgal_create_phase(const double* masks, int32_t L, int32_t n, const double* b, double alpha,
                        const scgal_params* params, scgal_t* out);
 
+/* Fourier-ptychography phase retrieval SDP (Section 7.4, App. F.2): C = I,
+ * tr X <= alpha, A_i = a_i a_i* with a_{j m + l} = W*_m(l, :) Phi_j, where
+ * x in C^n, n = N^2, is the Fourier-domain image (row-major N x N), W_m the
+ * 2-D M x M DFT (m = M^2, unnormalised, low-resolution pixels row-major) and
+ * Phi_j selects the M x M window of illumination j = kr K + kc (K = N / s,
+ * 0 <= kr, kc < K) starting at (kr s, kc s), pixel indices mod N, times the
+ * pupil: (Phi_j x)[r M + c] = pupil[r M + c] x[((kr s + r) mod N) N + (kc s + c) mod N].
+ *   pupil: M*M complex128 values as interleaved (re, im) doubles, row-major;
+ *          every entry must have modulus 1 (checked: SCGAL_EINVAL).
+ *   M a power of two, 2 <= M <= 64; s >= 1 divides N; M <= N <= 8192;
+ *   L m = K^2 M^2 < 2^31; params->R <= n (SCGAL_EINVAL).
+ *   b: K^2 M^2 doubles (finite), window-major, b[j m + l] = |(W*_m Phi_j chi)_l|^2.
+ *   alpha: <= 0 selects alpha = 1.5 (Section 7.4.2, for a unit-norm signal).
+ * With the periodic windows every row of the Gram matrix |a_i* a_k|^2 sums to
+ * the same value, so ||A|| = M sum_k |[0, M) cap ([k s, k s + M) mod N)|
+ * exactly (the scaling of Eq. 7.1 uses it).  Vectors are complex64
+ * (precision 32) or complex128 (precision 64).  pupil and b may be host or
+ * device pointers; the library copies them. */
+int scgal_create_ptycho(const double* pupil, int32_t M, int32_t N, int32_t s, const double* b, double alpha,
+                        const scgal_params* params, scgal_t* out);
+
 /* One SketchyCGAL iteration (Alg. 6.1 loop body): form D_t = C + A*(y + beta(z-b)),
  * ApproxMinEvec (Alg. 4.1, stored basis), z / sketch / objective updates
  * (Eq. 6.2), dual step (Eq. 6.3-6.4).  Blocks until done; *out (may be NULL)

@@ -16,6 +16,7 @@
 
 namespace scgal {
 template <typename V> int prepare_phase_kernels(const KP<V>& p);   // k_phase.cu
+template <typename V> int prepare_fp_kernels(const KP<V>& p);      // k_phase.cu
 }
 
 using namespace scgal;
@@ -466,6 +467,106 @@ int phase_build(scgal_ctx* h, const double* masks, const double* b) {
     return setup_state<V>(h);
 }
 
+// Fourier ptychography: pupil, window geometry, the per-coordinate window
+// coverage table, the closed-form ||A|| and the scaled measurements (natural
+// order j m + l).
+template <typename V>
+int ptycho_build(scgal_ctx* h, const double* pupil, const double* b, int M, int N, int s) {
+    typedef typename VT<V>::R R;
+    new_kp<V>(h);
+    KP<V>& p = kp<V>(h);
+    const int K = N / s, L = K * K, m = M * M, n = N * N;
+    const long long d = (long long)L * m;
+    std::vector<double> hp((size_t)2 * m), hb((size_t)d);
+    CUDA_TRY(h, cudaMemcpy(hp.data(), pupil, sizeof(double) * 2 * m, cudaMemcpyDefault));
+    CUDA_TRY(h, cudaMemcpy(hb.data(), b, sizeof(double) * d, cudaMemcpyDefault));
+    for (int i = 0; i < m; ++i)
+        if (!(std::fabs(std::hypot(hp[2 * i], hp[2 * i + 1]) - 1.0) <= 1e-9))
+            return set_err(h, SCGAL_EINVAL, "pupil entries must have modulus 1");
+    double nb2 = 0.0;
+    for (long long i = 0; i < d; ++i) {
+        if (!std::isfinite(hb[i])) return set_err(h, SCGAL_EINVAL, "non-finite measurement");
+        nb2 += hb[i] * hb[i];
+    }
+    int lg = 0;
+    while ((1 << lg) < M) ++lg;
+    p.fpN = N;
+    p.fpM = M;
+    p.fpS = s;
+    p.fpK = K;
+    p.fpLogM = lg;
+    p.fpCM = (M + s - 1) / s + 1;
+    std::vector<int2> cov((size_t)N * p.fpCM, make_int2(-1, -1));
+    for (int g = 0; g < N; ++g) {
+        int cnt = 0;
+        for (int k = 0; k < K; ++k) {
+            const int off = ((g - k * s) % N + N) % N;
+            if (off < M) {
+                if (cnt >= p.fpCM) return set_err(h, SCGAL_EINVAL, "window coverage table overflow");
+                cov[(size_t)g * p.fpCM + cnt++] = make_int2(k, off);
+            }
+        }
+    }
+    long long ovsum = 0;   // sum_k |[0, M) cap ([k s, k s + M) mod N)|
+    for (int k = 0; k < K; ++k)
+        for (int r = 0; r < M; ++r) ovsum += ((k * s + r) % N) < M ? 1 : 0;
+    Consts& c = h->c;
+    c.kind = KIND_PTYCHO;
+    c.n = n;
+    c.d = (int)d;
+    c.L = L;
+    c.nnz = 0;
+    c.lmo = (h->prm.lmo == SCGAL_LMO_DEFAULT) ? SCGAL_LMO_LEQ : h->prm.lmo;
+    h->normA = (double)M * (double)ovsum;
+    h->normC = std::sqrt((double)n);
+    const bool scale = h->prm.scale != 0;
+    c.sC = scale ? 1.0 / h->normC : 1.0;
+    c.sA = scale ? 1.0 / h->normA : 1.0;
+    c.alpha = scale ? 1.0 : h->alpha_orig;
+    c.b_const = 0;
+    c.obj_factor = scale ? h->alpha_orig * h->normC : 1.0;
+    c.z_factor = scale ? h->alpha_orig * h->normA : 1.0;
+    c.normb_orig = std::sqrt(nb2);
+    c.normA_s = scale ? 1.0 : h->normA;
+    fill_solver_consts(h);
+    const double bs = scale ? 1.0 / (h->alpha_orig * h->normA) : 1.0;
+    for (long long i = 0; i < d; ++i) hb[i] *= bs;
+    std::vector<V> hpup((size_t)m), htw((size_t)M);
+    for (int i = 0; i < m; ++i) {
+        hpup[i].x = (R)hp[2 * i];
+        hpup[i].y = (R)hp[2 * i + 1];
+    }
+    for (int k = 0; k < M; ++k) {
+        const double ang = -2.0 * M_PI * (double)k / (double)M;
+        htw[k].x = (R)std::cos(ang);
+        htw[k].y = (R)std::sin(ang);
+    }
+    V* dp = nullptr;
+    V* dtw = nullptr;
+    double* db = nullptr;
+    int2* dcov = nullptr;
+    ALLOC(h, dp, sizeof(V) * m);
+    ALLOC(h, dtw, sizeof(V) * M);
+    ALLOC(h, db, sizeof(double) * d);
+    ALLOC(h, dcov, sizeof(int2) * cov.size());
+    ALLOC(h, p.wvec, sizeof(R) * d);
+    ALLOC(h, p.fftbuf, sizeof(V) * d);
+    CUDA_TRY(h, cudaMemcpy(dp, hpup.data(), sizeof(V) * m, cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(dtw, htw.data(), sizeof(V) * M, cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(db, hb.data(), sizeof(double) * d, cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(dcov, cov.data(), sizeof(int2) * cov.size(), cudaMemcpyHostToDevice));
+    p.masks = dp;
+    p.twiddle = dtw;
+    p.b = db;
+    p.fpcov = dcov;
+    p.ynplanes = 1;
+    h->grid_elem = grid_for(d, SCGAL_BS, 4);
+    p.fpGrid = std::min(grid_for(n, SCGAL_BS, 4), h->grid_elem);
+    h->grid_spmv = std::max(h->grid_elem, L);   // the update kernel reduces over L blocks
+    if (prepare_fp_kernels<V>(p)) return set_err(h, SCGAL_ECUDA, "ptychography kernels: shared memory");
+    return setup_state<V>(h);
+}
+
 template <typename V>
 int read_scalars(scgal_ctx* h, DevScalars* out) {
     CUDA_TRY(h, cudaMemcpyAsync(out, kp<V>(h).sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
@@ -803,7 +904,8 @@ int do_get_state(scgal_ctx* h, double* z, double* y, double* S, double* scalars)
         if (h->cplx) {
             double* tmp = nullptr;
             CUDA_TRY(h, cudaMallocAsync((void**)&tmp, sizeof(double) * h->d, s));
-            phase_perm(srcs[q], tmp, h->d, h->n, p.n1, p.n2, 0, s);
+            if (h->kind == KIND_PHASE) phase_perm(srcs[q], tmp, h->d, h->n, p.n1, p.n2, 0, s);
+            else CUDA_TRY(h, cudaMemcpyAsync(tmp, srcs[q], sizeof(double) * h->d, cudaMemcpyDeviceToDevice, s));
             CUDA_TRY(h, cudaMemcpyAsync(dsts[q], tmp, sizeof(double) * h->d, cudaMemcpyDefault, s));
             CUDA_TRY(h, cudaFreeAsync(tmp, s));
         } else {
@@ -844,7 +946,8 @@ int do_set_state(scgal_ctx* h, const double* z, const double* y, const double* S
             double* tmp = nullptr;
             CUDA_TRY(h, cudaMallocAsync((void**)&tmp, sizeof(double) * h->d, s));
             if ((rc = copy_in(h, tmp, srcs[q], sizeof(double) * h->d))) return rc;
-            phase_perm(tmp, dsts[q], h->d, h->n, p.n1, p.n2, 1, s);
+            if (h->kind == KIND_PHASE) phase_perm(tmp, dsts[q], h->d, h->n, p.n1, p.n2, 1, s);
+            else CUDA_TRY(h, cudaMemcpyAsync(dsts[q], tmp, sizeof(double) * h->d, cudaMemcpyDeviceToDevice, s));
             CUDA_TRY(h, cudaFreeAsync(tmp, s));
         } else if ((rc = copy_in(h, dsts[q], srcs[q], sizeof(double) * h->d))) {
             return rc;
@@ -1129,6 +1232,35 @@ int scgal_create_phase(const double* masks, int32_t L, int32_t n, const double* 
     h->trace_correct = (params->trace_correct < 0) ? (lmo == SCGAL_LMO_LEQ ? 0 : 1) : params->trace_correct;
     int rc = common_open(h);
     if (!rc) rc = (h->prec == 32) ? phase_build<float2>(h, masks, b) : phase_build<double2>(h, masks, b);
+    if (rc) {
+        free_ctx(h);
+        return rc;
+    }
+    *out = h;
+    return SCGAL_OK;
+}
+
+int scgal_create_ptycho(const double* pupil, int32_t M, int32_t N, int32_t s, const double* b, double alpha,
+                        const scgal_params* params, scgal_t* out) {
+    if (!out) return SCGAL_EINVAL;
+    *out = nullptr;
+    if (!pupil || !b || M < 2 || M > 64 || (M & (M - 1)) || s < 1 || N < M || N > 8192 || N % s) return SCGAL_EINVAL;
+    const long long K = N / s;
+    if (K * K * (long long)M * M >= (1ll << 31)) return SCGAL_EINVAL;
+    if (check_params(params)) return SCGAL_EINVAL;
+    if (params->R > N * N) return SCGAL_EINVAL;   // the n x R sketch of an n x n matrix
+    scgal_ctx* h = new_ctx(params, KIND_PTYCHO);
+    h->cplx = 1;
+    h->n = N * N;
+    h->L = (int)(K * K);
+    h->d = (int)(K * K * M * M);
+    h->R = params->R;
+    h->alpha_orig = (alpha > 0.0) ? alpha : 1.5;
+    const int lmo = (params->lmo == SCGAL_LMO_DEFAULT) ? SCGAL_LMO_LEQ : params->lmo;
+    h->trace_correct = (params->trace_correct < 0) ? (lmo == SCGAL_LMO_LEQ ? 0 : 1) : params->trace_correct;
+    int rc = common_open(h);
+    if (!rc) rc = (h->prec == 32) ? ptycho_build<float2>(h, pupil, b, M, N, s)
+                                  : ptycho_build<double2>(h, pupil, b, M, N, s);
     if (rc) {
         free_ctx(h);
         return rc;

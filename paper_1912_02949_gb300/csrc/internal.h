@@ -14,7 +14,7 @@
 
 namespace scgal {
 
-enum ProblemKind { KIND_MAXCUT = 0, KIND_PHASE = 1 };
+enum ProblemKind { KIND_MAXCUT = 0, KIND_PHASE = 1, KIND_PTYCHO = 2 };
 enum WeightKind { W_UNIT = 0, W_PM1 = 1, W_REAL = 2 };
 
 // Scalars of the current iteration, resident in device memory so that a
@@ -84,6 +84,12 @@ struct KP {
     int ph_rpb;         // rows per block in the row pass
     int ph_mb;          // masks per block in the last pass (ynplanes = ceil(L / ph_mb))
     int ynplanes;       // planes of ybuf summed to form D x (1 for MaxCut)
+    // Fourier ptychography (KIND_PTYCHO): N x N image, M x M windows at offsets
+    // (kr s, kc s) mod N, K = N / s windows per dimension; masks holds the pupil
+    int fpN, fpM, fpS, fpK, fpLogM;
+    int fpCM;           // entries per coordinate of fpcov
+    int fpGrid;         // blocks of the per-pixel gather (<= the partials' capacity)
+    const int2* fpcov;  // N x fpCM: the windows (k, offset in window) covering coordinate g; k < 0 ends
     // state
     double* z;
     double* y;

@@ -336,6 +336,14 @@ __global__ void k_wvec_from_w(KP<V> p, const double* w) {
     }
 }
 
+// w (FP64) -> sA w, natural order (Fourier ptychography).
+template <typename V>
+__global__ void k_wvec_nat(KP<V> p, const double* w) {
+    typedef typename VT<V>::R Rt;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.c.d; i += (long long)gridDim.x * blockDim.x)
+        p.wvec[i] = (Rt)(p.c.sA * w[i]);
+}
+
 // ---------------------------------------------------------------------------
 // transform tile, then the length-n2 (columns) or length-n1 (rows) twiddles
 template <typename V> static size_t col_smem(const KP<V>& p) {
@@ -354,6 +362,200 @@ static void forward_and_weight(const KP<V>& p, const V* x, const typename VT<V>:
 // Raises the passes' dynamic shared-memory limit to what this handle's tiles
 // need (above 48 KB for the wider tiles); called once per handle, before any
 // launch or capture.
+// ---------------------------------------------------------------------------
+// Fourier ptychography (Section 7.4, App. F.2).  Window j = (kr, kc) of the
+// N x N Fourier-domain image starts at (kr s, kc s), indices mod N; Phi_j
+// multiplies its M x M pixels by the pupil; W_m is the 2-D M x M DFT.
+//   D x = sC x + sum_j Phi_j^* W_m (w_j .* W*_m Phi_j x)      (w already holds sA)
+// One block per window runs both 2-D transforms in shared memory (two
+// M x (M + 1) tiles: the padded row stride keeps the column passes free of
+// bank conflicts); k_fp_gather then sums, for every pixel, the windows that
+// cover it in a fixed order (no atomics: results do not depend on scheduling).
+template <typename V> size_t fp_smem(const KP<V>& p) {
+    return sizeof(V) * (2 * (size_t)p.fpM * (p.fpM + 1) + (size_t)(p.fpM / 2 + 1));
+}
+
+// W*_m Phi_j x into tile a (natural 2-D frequency order, row stride M + 1).
+template <typename V>
+__device__ void fp_window_inverse(const KP<V>& p, const V* __restrict__ x, int j, V* a, const V* tws) {
+    const int N = p.fpN, M = p.fpM, lg = p.fpLogM, LD = M + 1;
+    const int kr = j / p.fpK, kc = j - kr * p.fpK;
+    const int r0 = kr * p.fpS, c0 = kc * p.fpS;   // < N
+    for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+        const int r = idx >> lg, c = idx & (M - 1);
+        int gr = r0 + r;
+        if (gr >= N) gr -= N;                     // r0 < N and r < M <= N
+        int gc = c0 + c;
+        if (gc >= N) gc -= N;
+        a[brev(r, lg) * LD + brev(c, lg)] = CX<V>::mul(p.masks[idx], x[(size_t)gr * N + gc]);
+    }
+    __syncthreads();
+    smem_fft<V>(a, lg, M, 1, LD, tws, +1);         // rows: conjugate DFT
+    smem_fft<V>(a, lg, M, LD, 1, tws, +1);         // columns
+}
+
+// fftbuf[j m + l] = (Phi_j^* W_m (w_j .* W*_m Phi_j x)) restricted to window j, l = r M + c.
+template <typename V>
+__global__ void __launch_bounds__(SCGAL_BS) k_fp_apply(KP<V> p, const V* __restrict__ x,
+                                                       const typename VT<V>::R* __restrict__ w) {
+    typedef typename VT<V>::R Rt;
+    extern __shared__ unsigned char smraw[];
+    const int M = p.fpM, lg = p.fpLogM, LD = M + 1, m = M * M;
+    V* a = reinterpret_cast<V*>(smraw);
+    V* b = a + (size_t)M * LD;
+    V* tws = b + (size_t)M * LD;
+    load_small_twiddles(tws, p.twiddle, lg, lg);
+    const int j = blockIdx.x;
+    fp_window_inverse<V>(p, x, j, a, tws);
+    const Rt* __restrict__ wj = w + (size_t)j * m;
+    for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+        const int r = idx >> lg, c = idx & (M - 1);
+        V v = a[r * LD + c];
+        const Rt ww = wj[idx];
+        v.x *= ww;
+        v.y *= ww;
+        b[brev(r, lg) * LD + brev(c, lg)] = v;
+    }
+    __syncthreads();
+    smem_fft<V>(b, lg, M, 1, LD, tws, -1);         // rows: DFT
+    smem_fft<V>(b, lg, M, LD, 1, tws, -1);         // columns
+    V* out = p.fftbuf + (size_t)j * m;
+    for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+        const int r = idx >> lg, c = idx & (M - 1);
+        out[idx] = CX<V>::cmul(p.masks[idx], b[r * LD + c]);   // conj(pupil) * .
+    }
+}
+
+// out = sC x + (sum over the windows covering each pixel); DOT: also reduce
+// Re<x, D x> and finish Lanczos step i.
+template <typename V, int DOT>
+__global__ void __launch_bounds__(SCGAL_BS) k_fp_gather(KP<V> p, const V* __restrict__ x, V* __restrict__ out, int i) {
+    typedef typename VT<V>::R Rt;
+    const int N = p.fpN, K = p.fpK, CM = p.fpCM, lg = p.fpLogM, n = p.c.n;
+    const Rt sC = (Rt)p.c.sC;
+    Rt dot = 0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int gr = e / N, gc = e - gr * N;
+        const int2* __restrict__ cr = p.fpcov + (size_t)gr * CM;
+        const int2* __restrict__ cc = p.fpcov + (size_t)gc * CM;
+        V acc = vzero<V>();
+        for (int u = 0; u < CM; ++u) {
+            const int2 ru = cr[u];
+            if (ru.x < 0) break;
+            for (int v = 0; v < CM; ++v) {
+                const int2 cv = cc[v];
+                if (cv.x < 0) break;
+                const V t = p.fftbuf[((size_t)(ru.x * K + cv.x) << (2 * lg)) + ((size_t)ru.y << lg) + cv.y];
+                acc.x += t.x;
+                acc.y += t.y;
+            }
+        }
+        const V xe = x[e];
+        V val;
+        val.x = sC * xe.x + acc.x;
+        val.y = sC * xe.y + acc.y;
+        out[e] = val;
+        if (DOT) dot += xe.x * val.x + xe.y * val.y;
+    }
+    if constexpr (DOT) {
+        double v[1] = {(double)dot};
+        __shared__ double tot[1];
+        if (grid_reduce<1>(v, p.partials, p.ticket, tot)) finish_lanczos_step(p, i, tot[0]);
+    }
+}
+
+// Primal update of the iteration (Eq. 6.2): z <- (1 - eta) z + eta A(alpha v v*)
+// with A(v v*) = |W*_m Phi_j v|^2 per window, S <- (1 - eta) S + eta alpha v
+// (v* Omega) / ||v||^2, p and tau, and the dual step size (Eq. 6.4; with the
+// slack wbar for K = {u <= b}, Alg. D.1).  One block per window.
+template <typename V>
+__global__ void __launch_bounds__(SCGAL_BS) k_fp_update(KP<V> p) {
+    typedef typename VT<V>::R Rt;
+    DevScalars* sc = p.sc;
+    if (sc->converged) return;
+    extern __shared__ unsigned char smraw[];
+    const int M = p.fpM, lg = p.fpLogM, LD = M + 1, m = M * M;
+    V* a = reinterpret_cast<V*>(smraw);
+    V* tws = a + 2 * (size_t)M * LD;
+    load_small_twiddles(tws, p.twiddle, lg, lg);
+    const int j = blockIdx.x;
+    fp_window_inverse<V>(p, p.vbuf, j, a, tws);
+    const double eta = sc->eta, nv2 = sc->nv2;
+    const int take = sc->take_h;
+    const double zc = take ? eta * p.c.alpha * p.c.sA / nv2 : 0.0;
+    const double betap = p.c.beta0 * sqrt((double)(sc->t + 2));   // beta_{t+1}: wbar of Alg. D.1
+    double a_nzb = 0.0, a_yzb = 0.0, a_yy = 0.0;
+    for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+        const int r = idx >> lg, c = idx & (M - 1);
+        const size_t i = (size_t)j * m + idx;
+        const V X = a[r * LD + c];
+        const double a2 = (double)X.x * X.x + (double)X.y * X.y;
+        const double zi = fma(1.0 - eta, p.z[i], zc * a2);
+        p.z[i] = zi;
+        const double zb = zi - (p.c.kleq ? fmin(zi + p.y[i] / betap, p.b[i]) : p.b[i]);
+        a_nzb = fma(zb, zb, a_nzb);
+        if (p.c.K_finite) {
+            const double yi = p.y[i];
+            a_yzb = fma(yi, zb, a_yzb);
+            a_yy = fma(yi, yi, a_yy);
+        }
+    }
+    // sketch update (grid-stride over n R)
+    const int R = p.c.R, n = p.c.n;
+    __shared__ V rr[SCGAL_RMAX];
+    if (threadIdx.x < R) {
+        rr[threadIdx.x].x = (Rt)sc->r[2 * threadIdx.x];
+        rr[threadIdx.x].y = (Rt)sc->r[2 * threadIdx.x + 1];
+    }
+    __syncthreads();
+    const Rt sfac = take ? (Rt)(eta * p.c.alpha / nv2) : (Rt)0;
+    const Rt om1 = (Rt)(1.0 - eta);
+    const long long nR = (long long)n * R;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nR; k += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(k / R);
+        const int cI = (int)(k - (long long)e * R);
+        const V vr = CX<V>::mul(p.vbuf[e], rr[cI]);
+        V sv = p.S[k];
+        sv.x = om1 * sv.x + sfac * vr.x;
+        sv.y = om1 * sv.y + sfac * vr.y;
+        p.S[k] = sv;
+    }
+    double red[3] = {a_nzb, a_yzb, a_yy};
+    __shared__ double tot[3];
+    if (grid_reduce<3>(red, p.partials, p.ticket, tot)) {
+        if (threadIdx.x == 0) {
+            const Consts& c = p.c;
+            sc->vCv = c.sC;
+            sc->p = (1.0 - eta) * sc->p + (take ? eta * c.alpha * c.sC : 0.0);
+            sc->tau = (1.0 - eta) * sc->tau + (take ? eta * c.alpha : 0.0);
+            const double nzb2 = tot[0];
+            const long long t = sc->t;
+            double gamma = (nzb2 == 0.0)
+                               ? c.beta0
+                               : fmin(c.beta0, 4.0 * c.alpha * c.alpha * c.beta0 * c.normA_s * c.normA_s /
+                                                   (pow((double)(t + 1), 1.5) * nzb2));
+            if (c.K_finite) {
+                const double yy = tot[2] + 2.0 * gamma * tot[1] + gamma * gamma * nzb2;
+                if (sqrt(yy) > c.K) gamma = 0.0;
+            }
+            sc->gamma = gamma;
+            sc->nzb2_new = nzb2;
+            p.hist[(t - 1) % c.hist_cap].gamma = gamma;
+        }
+    }
+}
+
+template <typename V> int prepare_fp_kernels(const KP<V>& p) {
+    const int sm = (int)fp_smem(p);
+    cudaError_t e = cudaFuncSetAttribute(k_fp_apply<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fp_update<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SCGAL_ECUDA;
+    }
+    return SCGAL_OK;
+}
+
 template <typename V> int prepare_phase_kernels(const KP<V>& p) {
     const int cs = (int)col_smem(p), rs = (int)row_smem(p);
     cudaError_t e = cudaFuncSetAttribute(k_ph_p1<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs);
@@ -370,6 +572,11 @@ template <typename V> int prepare_phase_kernels(const KP<V>& p) {
 
 template <typename V> void launch_phase_step(const KP<V>& p, int i, cudaStream_t s) {
     const V* x = p.basis + (size_t)i * p.ldb;
+    if (p.c.kind == KIND_PTYCHO) {
+        k_fp_apply<V><<<p.c.L, SCGAL_BS, fp_smem(p), s>>>(p, x, p.wvec);
+        k_fp_gather<V, 1><<<p.fpGrid, SCGAL_BS, 0, s>>>(p, x, p.ybuf, i);
+        return;
+    }
     // the column and row passes skip nothing on breakdown; only their cost is wasted
     forward_and_weight<V>(p, x, p.wvec, s);
     k_ph_p3<V, 1><<<dim3(p.n1 / p.ph_tc, p.ynplanes), SCGAL_BS, col_smem(p), s>>>(p, x, p.ybuf, i);
@@ -377,18 +584,31 @@ template <typename V> void launch_phase_step(const KP<V>& p, int i, cudaStream_t
 
 template <typename V> void launch_phase_update(const KP<V>& p, int grid, cudaStream_t s) {
     (void)grid;
+    if (p.c.kind == KIND_PTYCHO) {
+        k_fp_update<V><<<p.c.L, SCGAL_BS, fp_smem(p), s>>>(p);
+        return;
+    }
     k_ph_p1<V><<<dim3(p.n1 / p.ph_tc, p.c.L), SCGAL_BS, col_smem(p), s>>>(p, p.vbuf);
     k_ph_p2<V, 1><<<dim3(p.n2 / p.ph_rpb, p.c.L), SCGAL_BS, row_smem(p), s>>>(p, nullptr);
 }
 
 template <typename V>
 void launch_apply_D_phase(const KP<V>& p, const V* x, V* out, const typename VT<V>::R* w, cudaStream_t s) {
+    if (p.c.kind == KIND_PTYCHO) {
+        k_fp_apply<V><<<p.c.L, SCGAL_BS, fp_smem(p), s>>>(p, x, w);
+        k_fp_gather<V, 0><<<p.fpGrid, SCGAL_BS, 0, s>>>(p, x, out, 0);
+        return;
+    }
     forward_and_weight<V>(p, x, w, s);
     k_ph_p3<V, 0><<<dim3(p.n1 / p.ph_tc, p.ynplanes), SCGAL_BS, col_smem(p), s>>>(p, x, p.ybuf, 0);
     k_plane_sum<V><<<(p.c.n + 255) / 256, 256, 0, s>>>(p.ybuf, p.ynplanes, p.ldb, p.c.n, out);
 }
 
 template <typename V> void launch_wvec_from_w(const KP<V>& p, int grid, const double* w, cudaStream_t s) {
+    if (p.c.kind == KIND_PTYCHO) {   // measurements stay in their natural order
+        k_wvec_nat<V><<<grid, SCGAL_BS, 0, s>>>(p, w);
+        return;
+    }
     k_wvec_from_w<V><<<grid, SCGAL_BS, 0, s>>>(p, w);
 }
 
@@ -408,6 +628,7 @@ void phase_perm(const double* in, double* out, long long d, int n, int n1, int n
 
 #define INST(V)                                                                                           \
     template int prepare_phase_kernels<V>(const KP<V>&);                                                  \
+    template int prepare_fp_kernels<V>(const KP<V>&);                                                     \
     template void launch_phase_step<V>(const KP<V>&, int, cudaStream_t);                                  \
     template void launch_phase_update<V>(const KP<V>&, int, cudaStream_t);                                \
     template void launch_apply_D_phase<V>(const KP<V>&, const V*, V*, const typename VT<V>::R*, cudaStream_t); \

@@ -82,6 +82,8 @@ _PROTOS = {
                                     POINTER(scgal_params), POINTER(c_void_p)]),
     "scgal_create_phase": (c_int, [c_void_p, c_int32, c_int32, c_void_p, c_double, POINTER(scgal_params),
                                    POINTER(c_void_p)]),
+    "scgal_create_ptycho": (c_int, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_double, POINTER(scgal_params),
+                                    POINTER(c_void_p)]),
     "scgal_step": (c_int, [c_void_p, POINTER(scgal_stats)]),
     "scgal_solve": (c_int, [c_void_p, c_int64, POINTER(scgal_stats)]),
     "scgal_reconstruct": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int64)]),
@@ -203,6 +205,21 @@ def scgal_create_phase(masks, L: int, n: int, b, alpha: float = 0.0, params: scg
     rc = load().scgal_create_phase(_ptr(m), int(L), int(n), _ptr(b), float(alpha), ctypes.byref(params), ctypes.byref(h))
     _check(rc, "scgal_create_phase")
     return Handle(h, int(n), int(L) * int(n), params.R, True)
+
+
+def scgal_create_ptycho(pupil, M: int, N: int, s: int, b, alpha: float = 0.0,
+                        params: scgal_params | None = None) -> Handle:
+    """pupil: complex128[M * M] (or float64[M * M, 2]); b: float64[(N / s)^2 * M * M]."""
+    params = params or scgal_params_default()
+    pp = pupil
+    if isinstance(pp, np.ndarray) and np.iscomplexobj(pp):
+        pp = np.ascontiguousarray(pp.astype(np.complex128)).view(np.float64)
+    h = c_void_p()
+    rc = load().scgal_create_ptycho(_ptr(pp), int(M), int(N), int(s), _ptr(b), float(alpha), ctypes.byref(params),
+                                    ctypes.byref(h))
+    _check(rc, "scgal_create_ptycho")
+    K = int(N) // int(s)
+    return Handle(h, int(N) * int(N), K * K * int(M) * int(M), params.R, True)
 
 
 def scgal_step(h: Handle) -> dict:

@@ -91,5 +91,11 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     m = (ctypes.c_double * 64)()
     big = S.scgal_params_default(R=17)
     assert lib.scgal_create_phase(m, 1, 16, m, 0.0, ctypes.byref(big), ctypes.byref(h)) == S.SCGAL_EINVAL
+    # ptychography geometry is checked before any CUDA call: M a power of two in
+    # [2, 64], s | N, M <= N
+    pp = (ctypes.c_double * 128)()
+    good = S.scgal_params_default(R=2)
+    for (M, N, s_) in ((6, 12, 3), (8, 12, 5), (16, 8, 2), (128, 256, 2), (1, 4, 2)):
+        assert lib.scgal_create_ptycho(pp, M, N, s_, pp, 0.0, ctypes.byref(good), ctypes.byref(h)) == S.SCGAL_EINVAL
     assert lib.scgal_strerror(S.SCGAL_ENUMERIC).decode() == "numerical failure"
     assert lib.scgal_step(None, None) == S.SCGAL_EINVAL

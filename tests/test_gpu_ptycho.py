@@ -1,0 +1,113 @@
+"""GPU parity of the Fourier-ptychography operator (Section 7.4, App. F.2)
+against the FP64 oracle (numpy FFTs), through the C ABI.  Tolerances as for
+coded diffraction (test_gpu_phase): one D-matvec 1e-5 (FP32) / 1e-12 (FP64),
+the first iterations step for step, end-of-run objective and infeasibility
+1e-3 / 1e-7, and the recovered image within the oracle's own 2e-2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.problems import PtychoProblem
+from oracle.rounding import phase_error, phase_round
+from oracle.sketchycgal import sketchy_cgal
+
+pytestmark = pytest.mark.gpu
+
+TOL_MV = {32: 1e-5, 64: 1e-12}
+TOL_XI = {32: 1e-4, 64: 1e-10}
+TOL_E2E = {32: 1e-3, 64: 1e-7}
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_1912_02949_gb300 import build, scgal
+    build.build()
+    scgal.load()
+    return scgal
+
+
+def _pair(S, N, M, s, prec, R=5, T_max=100, seed=0, **kw):
+    pd = W.ptycho_problem(N, M, s, seed=seed)
+    h = S.scgal_create_ptycho(pd.pupil, M, N, s, pd.b, 0.0,
+                              S.scgal_params_default(R=R, T_max=T_max, precision=prec, seed=seed, **kw))
+    return pd, h, PtychoProblem(N, M, s, pd.pupil, pd.b)
+
+
+def _relerr(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("N,M,s", [(12, 4, 3), (16, 8, 2), (40, 8, 5), (64, 16, 8), (320, 64, 20)])
+def test_apply_D_matches_oracle(S, N, M, s, prec):
+    pd, h, prob = _pair(S, N, M, s, prec)
+    r = np.random.default_rng(N + M)
+    x = r.standard_normal(N * N) + 1j * r.standard_normal(N * N)
+    w = r.standard_normal(prob.d)
+    yg = S.scgal_apply_D(h, x, w)
+    yo = prob.C_apply(x) + prob.Astar_apply(w, x)
+    assert _relerr(yg, yo) <= TOL_MV[prec]
+    info = S.scgal_get_info(h)
+    assert info["is_complex"] == 1 and math.isclose(info["normA"], prob.normA) and info["d"] == prob.d
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_first_iterations_and_end_to_end(S, prec):
+    N, M, s, T = 16, 8, 2, 300
+    pd, h, prob = _pair(S, N, M, s, prec, T_max=T)
+    ref = sketchy_cgal(prob, R=5, T=T, seed=0)
+    rc, last = S.scgal_solve(h, T)
+    hist = S.scgal_history(h, 1, T)
+    assert [r["q"] for r in hist] == [r["q"] for r in ref.history]
+    for rg, rr in zip(hist[:3], ref.history[:3]):
+        assert abs(rg["xi"] - rr["xi"]) <= TOL_XI[prec] * abs(rr["xi"])
+        assert abs(rg["p"] - rr["p_orig"]) <= TOL_XI[prec] * max(abs(rr["p_orig"]), 1e-3)
+        assert abs(rg["gamma"] - rr["gamma"]) <= TOL_XI[prec] * abs(rr["gamma"])
+    ro = ref.history[-1]
+    assert abs(last["p"] - ro["p_orig"]) <= TOL_E2E[prec] * abs(ro["p_orig"])
+    assert abs(last["infeas"] - ro["infeas"]) <= max(TOL_E2E[prec] * ro["infeas"], 1e-9)
+    U, lam, err, _ = S.scgal_reconstruct(h, want_cut=False)
+    np.testing.assert_allclose(lam[0], ref.Lam[0], rtol=(1e-3 if prec == 32 else 1e-7))
+
+
+def test_recovers_image(S):
+    """16 intensities per real unknown, T = 1500 (the oracle's own pin reaches 2e-2)."""
+    N, M, s, T = 16, 8, 2, 1500
+    pd, h, prob = _pair(S, N, M, s, 32, T_max=T)
+    S.scgal_solve(h, T)
+    U, lam, err, _ = S.scgal_reconstruct(h, want_cut=False)
+    assert phase_error(phase_round(U.T, lam), pd.chi) < 2e-2
+
+
+def test_full_size_first_iterations(S):
+    """N = 320 (n = 102,400), 64 x 64 windows on a 16 x 16 grid: two FP64 iterations."""
+    N, M, s, T = 320, 64, 20, 2
+    pd, h, prob = _pair(S, N, M, s, 64, T_max=1000)
+    ref = sketchy_cgal(prob, R=5, T=T, seed=0)
+    S.scgal_solve(h, T)
+    for rg, rr in zip(S.scgal_history(h, 1, T), ref.history):
+        assert rg["q"] == rr["q"]
+        assert abs(rg["xi"] - rr["xi"]) <= 1e-9 * abs(rr["xi"])
+        assert abs(rg["p"] - rr["p_orig"]) <= 1e-9 * max(abs(rr["p_orig"]), 1e-3)
+
+
+def test_state_roundtrip_natural_order(S):
+    pd, h, prob = _pair(S, 16, 8, 4, 64)
+    r = np.random.default_rng(1)
+    z = r.standard_normal(prob.d)
+    y = r.standard_normal(prob.d)
+    S.scgal_set_state(h, z=z, y=y, t=3)
+    st = S.scgal_get_state(h)
+    np.testing.assert_array_equal(st["z"], z)
+    np.testing.assert_array_equal(st["y"], y)
+
+
+def test_invalid_pupil_rejected(S):
+    pd = W.ptycho_problem(16, 8, 4, seed=0)
+    bad = pd.pupil.copy()
+    bad[5] = 0.5
+    with pytest.raises(S.ScgalError):
+        S.scgal_create_ptycho(bad, 8, 16, 4, pd.b, 0.0, S.scgal_params_default(R=3))
