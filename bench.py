@@ -465,6 +465,20 @@ def profile_phase(T: int):
     h.close()
 
 
+def profile_ptycho(T: int):
+    """One untimed FP32 solve of the Fourier-ptychography workload (for ncu captures)."""
+    import workloads as W
+    from paper_1912_02949_gb300 import scgal as S
+    S.load()
+    N, M, s = 320, 64, 20
+    pd = W.ptycho_problem(N, M, s, seed=SEED)
+    h = S.scgal_create_ptycho(pd.pupil, M, N, s, pd.b, 0.0, S.scgal_params_default(R=5, T_max=T, precision=32, seed=SEED))
+    t0 = time.perf_counter()
+    rc, last = S.scgal_solve(h, T)
+    print(json.dumps({"T": T, "seconds": time.perf_counter() - t0, "relgap": last["relgap"]}))
+    h.close()
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -492,6 +506,8 @@ def main():
                     help="one untimed FP32 solve of T iterations of the workload (for ncu captures)")
     ap.add_argument("--profile-phase", action="store_true",
                     help="one untimed FP32 solve of T iterations of the phase-retrieval workload (for ncu captures)")
+    ap.add_argument("--profile-ptycho", action="store_true",
+                    help="one untimed FP32 solve of T iterations of the ptychography workload (for ncu captures)")
     args = ap.parse_args()
     if args.cpu_sample:
         print(json.dumps(cpu_sample(args.cpu_sample, args.cpu_reps)))
@@ -504,6 +520,9 @@ def main():
         return
     if args.profile_phase:
         profile_phase(args.T)
+        return
+    if args.profile_ptycho:
+        profile_ptycho(args.T)
         return
     if args.profile_serve:
         from paper_1912_02949_gb300 import scgal as S
