@@ -431,6 +431,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_apply(KP<V> p, const V* __restr
 template <typename V, int DOT>
 __global__ void __launch_bounds__(SCGAL_BS) k_fp_gather(KP<V> p, const V* __restrict__ x, V* __restrict__ out, int i) {
     typedef typename VT<V>::R Rt;
+    constexpr int CF = 6;   // coverage entries held in registers (the common case: ceil(M/s) + 1 <= 6)
     const int N = p.fpN, K = p.fpK, CM = p.fpCM, lg = p.fpLogM, n = p.c.n;
     const Rt sC = (Rt)p.c.sC;
     Rt dot = 0;
@@ -439,15 +440,36 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_gather(KP<V> p, const V* __rest
         const int2* __restrict__ cr = p.fpcov + (size_t)gr * CM;
         const int2* __restrict__ cc = p.fpcov + (size_t)gc * CM;
         V acc = vzero<V>();
-        for (int u = 0; u < CM; ++u) {
-            const int2 ru = cr[u];
-            if (ru.x < 0) break;
-            for (int v = 0; v < CM; ++v) {
-                const int2 cv = cc[v];
-                if (cv.x < 0) break;
-                const V t = p.fftbuf[((size_t)(ru.x * K + cv.x) << (2 * lg)) + ((size_t)ru.y << lg) + cv.y];
-                acc.x += t.x;
-                acc.y += t.y;
+        if (CM <= CF) {
+            // both coverage lists in registers first, so the window loads below are
+            // independent (same terms in the same order as the loop further down)
+            int2 ru[CF], cv[CF];
+#pragma unroll
+            for (int u = 0; u < CF; ++u) {
+                ru[u] = (u < CM) ? cr[u] : make_int2(-1, 0);
+                cv[u] = (u < CM) ? cc[u] : make_int2(-1, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < CF; ++u)
+#pragma unroll
+                for (int v = 0; v < CF; ++v)
+                    if (ru[u].x >= 0 && cv[v].x >= 0) {
+                        const V t = p.fftbuf[((size_t)(ru[u].x * K + cv[v].x) << (2 * lg)) + ((size_t)ru[u].y << lg) +
+                                             cv[v].y];
+                        acc.x += t.x;
+                        acc.y += t.y;
+                    }
+        } else {
+            for (int u = 0; u < CM; ++u) {
+                const int2 ru = cr[u];
+                if (ru.x < 0) break;
+                for (int v = 0; v < CM; ++v) {
+                    const int2 cv = cc[v];
+                    if (cv.x < 0) break;
+                    const V t = p.fftbuf[((size_t)(ru.x * K + cv.x) << (2 * lg)) + ((size_t)ru.y << lg) + cv.y];
+                    acc.x += t.x;
+                    acc.y += t.y;
+                }
             }
         }
         const V xe = x[e];
