@@ -381,13 +381,30 @@ __device__ void fp_window_inverse(const KP<V>& p, const V* __restrict__ x, int j
     const int N = p.fpN, M = p.fpM, lg = p.fpLogM, LD = M + 1;
     const int kr = j / p.fpK, kc = j - kr * p.fpK;
     const int r0 = kr * p.fpS, c0 = kc * p.fpS;   // < N
-    for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-        const int r = idx >> lg, c = idx & (M - 1);
-        int gr = r0 + r;
-        if (gr >= N) gr -= N;                     // r0 < N and r < M <= N
-        int gc = c0 + c;
-        if (gc >= N) gc -= N;
-        a[brev(r, lg) * LD + brev(c, lg)] = CX<V>::mul(p.masks[idx], x[(size_t)gr * N + gc]);
+    constexpr int UL = 8;                          // loads issued before any is used
+    for (int base = threadIdx.x; base < M * M; base += blockDim.x * UL) {
+        V xv[UL], pv[UL];
+#pragma unroll
+        for (int u = 0; u < UL; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < M * M) {
+                const int r = idx >> lg, c = idx & (M - 1);
+                int gr = r0 + r;
+                if (gr >= N) gr -= N;             // r0 < N and r < M <= N
+                int gc = c0 + c;
+                if (gc >= N) gc -= N;
+                xv[u] = x[(size_t)gr * N + gc];
+                pv[u] = p.masks[idx];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UL; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < M * M) {
+                const int r = idx >> lg, c = idx & (M - 1);
+                a[brev(r, lg) * LD + brev(c, lg)] = CX<V>::mul(pv[u], xv[u]);
+            }
+        }
     }
     __syncthreads();
     smem_fft<V>(a, lg, M, 1, LD, tws, +1);         // rows: conjugate DFT
@@ -408,13 +425,25 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_apply(KP<V> p, const V* __restr
     const int j = blockIdx.x;
     fp_window_inverse<V>(p, x, j, a, tws);
     const Rt* __restrict__ wj = w + (size_t)j * m;
-    for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
-        const int r = idx >> lg, c = idx & (M - 1);
-        V v = a[r * LD + c];
-        const Rt ww = wj[idx];
-        v.x *= ww;
-        v.y *= ww;
-        b[brev(r, lg) * LD + brev(c, lg)] = v;
+    constexpr int UL = 8;
+    for (int base = threadIdx.x; base < m; base += blockDim.x * UL) {
+        Rt wv[UL];
+#pragma unroll
+        for (int u = 0; u < UL; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < m) wv[u] = wj[idx];
+        }
+#pragma unroll
+        for (int u = 0; u < UL; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < m) {
+                const int r = idx >> lg, c = idx & (M - 1);
+                V v = a[r * LD + c];
+                v.x *= wv[u];
+                v.y *= wv[u];
+                b[brev(r, lg) * LD + brev(c, lg)] = v;
+            }
+        }
     }
     __syncthreads();
     smem_fft<V>(b, lg, M, 1, LD, tws, -1);         // rows: DFT
