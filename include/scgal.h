@@ -91,6 +91,11 @@ typedef struct {
     int32_t  omega;         /* SCGAL_OMEGA_*: how the n x R test matrix of the sketch is
                                held (default STORED) */
     int32_t  kset;          /* SCGAL_K_*: the constraint set K of A(X) in K (default EQ) */
+    int32_t  tune;          /* 1: MaxCut handles pick the D-matvec grid by timing the
+                               candidates (2, 4, 6, 8 blocks per SM) on their own graph at
+                               create, cached per (precision, weight kind, log2 n, log2 of
+                               the average degree) in the process; results then differ from
+                               the fixed shape (6 blocks per SM, default 0) by rounding */
 } scgal_params;
 
 /* One iteration record (Alg. 6.1 step t; stopping values of Eq. E.1 for the
@@ -119,7 +124,7 @@ typedef struct {
     double  normC, normA; /* ||C||_F and ||A|| of the original data */
     int64_t device_bytes; /* device memory held by the handle */
     int32_t spmv_group;   /* lanes per CSR row chosen for the D-matvec */
-    int32_t reserved;
+    int32_t spmv_grid;    /* blocks of the MaxCut D-matvec grid (fixed or tuned); 0 otherwise */
 } scgal_info;
 
 /* Fill *p with the defaults listed above. */

@@ -86,6 +86,13 @@ int grid_for(long long work, int per_block, int cap_per_sm) {
     return (int)g;
 }
 
+// Candidate grids of the D-matvec autotuner in blocks per SM; the fixed shape
+// without tuning is TUNE_DEFAULT_CAP.
+constexpr int TUNE_CAPS[] = {2, 4, 6, 8};
+constexpr int TUNE_NCAPS = 4;
+constexpr int TUNE_DEFAULT_CAP = 6;
+template <typename V> int tune_spmv_grid(scgal_ctx* h);
+
 // ---------------------------------------------------------------------------
 template <typename V>
 void enqueue_iteration(scgal_ctx* h, int q, cudaStream_t s) {
@@ -215,6 +222,7 @@ int check_params(const scgal_params* p) {
     if (p->check_every < 1) return SCGAL_EINVAL;
     if (p->omega != SCGAL_OMEGA_STORED && p->omega != SCGAL_OMEGA_REGEN) return SCGAL_EINVAL;
     if (p->kset != SCGAL_K_EQ && p->kset != SCGAL_K_LEQ) return SCGAL_EINVAL;
+    if (p->tune != 0 && p->tune != 1) return SCGAL_EINVAL;
     if (p->device >= 0) {
         int count = 0;
         if (cudaGetDeviceCount(&count) != cudaSuccess || p->device >= count) {
@@ -373,9 +381,12 @@ int maxcut_build(scgal_ctx* h, const int32_t* row_ptr, const int32_t* col, const
     // launch shapes: the D-matvec takes a warp per 32 rows (8 chunks of rows in
     // flight per block), the streaming kernels 16-byte groups per thread
     h->spmv_group = 32;
-    h->grid_spmv = grid_for(n, SCGAL_BS, 6);
+    // with tuning on, the reduction partials are sized for the largest candidate grid
+    h->grid_spmv = grid_for(n, SCGAL_BS, h->prm.tune ? TUNE_CAPS[TUNE_NCAPS - 1] : TUNE_DEFAULT_CAP);
     h->grid_elem = grid_for((n + 3) / 4, SCGAL_BS, 8);
-    return setup_state<V>(h);
+    const int src = setup_state<V>(h);
+    if (src || !h->prm.tune) return src;
+    return tune_spmv_grid<V>(h);
 }
 
 template <typename V>
@@ -465,6 +476,90 @@ int phase_build(scgal_ctx* h, const double* masks, const double* b) {
     if (p2blocks > h->grid_spmv) h->grid_spmv = p2blocks;
     if (prepare_phase_kernels<V>(p)) return set_err(h, SCGAL_ECUDA, "phase-retrieval kernels: shared memory");
     return setup_state<V>(h);
+}
+
+// Launch-shape autotuner (params.tune): the MaxCut D-matvec k_spmv_step (a warp
+// per 32-row chunk, grid-stride over the chunks) is timed with CUDA events on
+// the handle's stream for each candidate grid of TUNE_CAPS blocks per SM, on the
+// handle's own graph and start vector with private iteration scalars (the
+// solver state is not touched: the step also writes D W_0 and omega_0, which the
+// first iteration rewrites), and the fastest is kept.  Results are cached per
+// (precision, weight kind, log2 n, log2 of the average degree) for the life of
+// the process, so repeated solves of one workload search once.  The grid
+// decides which rows each block's partial sums cover, so two grids give
+// results that differ by rounding; with tuning off (the default) the shape is
+// fixed and results are bitwise reproducible from run to run.
+struct TuneKey {
+    int prec, wkind, ln, ld;
+    bool operator<(const TuneKey& o) const {
+        if (prec != o.prec) return prec < o.prec;
+        if (wkind != o.wkind) return wkind < o.wkind;
+        if (ln != o.ln) return ln < o.ln;
+        return ld < o.ld;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;
+
+int ilog2_floor(long long v) {
+    int r = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+template <typename V>
+int tune_spmv_grid(scgal_ctx* h) {
+    const int n = h->n;
+    const TuneKey key{h->prec, h->c.wkind, ilog2_floor(n), ilog2_floor(std::max<long long>(1, h->nnz / n))};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            h->grid_spmv = grid_for(n, SCGAL_BS, it->second);
+            return SCGAL_OK;
+        }
+    }
+    cudaStream_t s = h->stream;
+    KP<V> q = kp<V>(h);
+    DevScalars* sc = nullptr;
+    CUDA_TRY(h, cudaMallocAsync((void**)&sc, sizeof(DevScalars), s));
+    CUDA_TRY(h, cudaMemsetAsync(sc, 0, sizeof(DevScalars), s));
+    q.sc = sc;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(h, cudaEventCreate(&e0));
+    CUDA_TRY(h, cudaEventCreate(&e1));
+    int best_cap = TUNE_DEFAULT_CAP;
+    float best_ms = 0.f;
+    constexpr int REPS = 10;
+    for (int k = 0; k < TUNE_NCAPS; ++k) {
+        const int g = grid_for(n, SCGAL_BS, TUNE_CAPS[k]);
+        launch_spmv_step<V>(q, g, h->spmv_group, 0, s);   // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < REPS; ++r) launch_spmv_step<V>(q, g, h->spmv_group, 0, s);
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cudaFreeAsync(sc, s);
+            return set_err(h, SCGAL_ECUDA, "CUDA error while tuning the D-matvec");
+        }
+        if (k == 0 || ms < best_ms) {
+            best_ms = ms;
+            best_cap = TUNE_CAPS[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_TRY(h, cudaFreeAsync(sc, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    h->grid_spmv = grid_for(n, SCGAL_BS, best_cap);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best_cap;
+    return SCGAL_OK;
 }
 
 // Fourier ptychography: pupil, window geometry, the per-coordinate window
@@ -1364,6 +1459,7 @@ int scgal_get_info(scgal_t h, scgal_info* out) {
     out->normA = h->normA;
     out->device_bytes = h->device_bytes;
     out->spmv_group = h->spmv_group;
+    out->spmv_grid = h->kind == KIND_MAXCUT ? h->grid_spmv : 0;
     return SCGAL_OK;
 }
 

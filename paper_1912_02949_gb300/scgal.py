@@ -39,7 +39,7 @@ class scgal_params(Structure):
     _fields_ = [("R", c_int32), ("T_max", c_int32), ("tol", c_double), ("beta0", c_double), ("K", c_double),
                 ("lmo", c_int32), ("scale", c_int32), ("trace_correct", c_int32), ("precision", c_int32),
                 ("seed", c_uint64), ("instance", c_uint32), ("check_every", c_int32), ("device", c_int32),
-                ("omega", c_int32), ("kset", c_int32)]
+                ("omega", c_int32), ("kset", c_int32), ("tune", c_int32)]
 
 
 class scgal_stats(Structure):
@@ -56,7 +56,7 @@ class scgal_info(Structure):
                 ("lmo", c_int32), ("trace_correct", c_int32), ("scale", c_int32), ("nnz", c_int64),
                 ("weight_kind", c_int32), ("qmax", c_int32), ("t", c_int64), ("alpha", c_double),
                 ("normC", c_double), ("normA", c_double), ("device_bytes", c_int64), ("spmv_group", c_int32),
-                ("reserved", c_int32)]
+                ("spmv_grid", c_int32)]
 
 
 class scgal_result(Structure):

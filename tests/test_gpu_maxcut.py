@@ -310,3 +310,26 @@ def test_full_size_torus2p23_matvec_and_first_iteration(S):
     assert math.isclose(st["z"].sum(), st["tau"], rel_tol=1e-5)
     assert math.isclose(st["tau"], 1.0, rel_tol=1e-12)
     h.close()
+
+
+def test_autotuned_grid_is_cached_and_leaves_the_state_alone(S):
+    """params.tune: the first handle times the candidate D-matvec grids (on its
+    own graph, private scalars) and caches the pick; a second handle of the same
+    shape reuses it without running the tuning launches.  Identical histories
+    show that the tuning launches did not disturb the first handle's state; the
+    tuned D-matvec matches the oracle like the fixed shape."""
+    g = W.er_graph(20000, 80000, seed=9, weights="pm1")
+    T = 40
+    a = _handle(S, g, 32, T_max=T, tune=1)
+    b = _handle(S, g, 32, T_max=T, tune=1)
+    ia, ib = S.scgal_get_info(a), S.scgal_get_info(b)
+    assert ia["spmv_grid"] == ib["spmv_grid"] > 0
+    S.scgal_solve(a, T)
+    S.scgal_solve(b, T)
+    assert S.scgal_history(a, 1, T) == S.scgal_history(b, 1, T)
+    prob = MaxCutProblem(g.n, g.i, g.j, g.w)
+    r = np.random.default_rng(2)
+    x = r.standard_normal(g.n)
+    w = r.standard_normal(g.n)
+    yo = prob.C_apply(x) + prob.Astar_apply(w, x)
+    assert _relerr(S.scgal_apply_D(b, x, w), yo) <= TOL_MV[32]
