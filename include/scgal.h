@@ -325,6 +325,15 @@ int scgal_server_create(size_t hbm_budget, int32_t max_slots, scgal_srv_t* out);
 int scgal_submit(scgal_srv_t s, const int32_t* row_ptr, const int32_t* col, const double* w,
                  int32_t n, int64_t nnz, const scgal_params* params, uint64_t* ticket);
 
+/* Queue a coded-diffraction phase-retrieval solve (arguments as
+ * scgal_create_phase; masks and b are copied before return; SCGAL_EINVAL for
+ * the same conditions).  It runs on its handle's own iteration graphs, in the
+ * same rounds as the batched MaxCut solves; its result has best_cut = 0 and
+ * objective = tr X in original units.  Non-blocking; SCGAL_EBUSY if the queue
+ * is full. */
+int scgal_submit_phase(scgal_srv_t s, const double* masks, int32_t L, int32_t n, const double* b,
+                       const scgal_params* params, uint64_t* ticket);
+
 /* Wait up to timeout_ms (0: just test, < 0: forever) for a request's result.
  * SCGAL_ETIMEOUT if it is not ready; the result is kept until read once. */
 int scgal_poll(scgal_srv_t s, uint64_t ticket, scgal_result* out, int32_t timeout_ms);

@@ -36,9 +36,12 @@ double now_ms() {
 
 struct Request {
     uint64_t id = 0;
-    std::vector<int32_t> row_ptr, col;
+    int kind = 0;                       // 0: MaxCut graph, 1: coded-diffraction phase retrieval
+    std::vector<int32_t> row_ptr, col;  // MaxCut
     std::vector<double> w;
     bool has_w = false;
+    std::vector<double> masks, b;       // phase retrieval: L x n masks (re, im), L n measurements
+    int32_t L = 0;
     int32_t n = 0;
     int64_t nnz = 0;
     scgal_params prm{};
@@ -72,6 +75,24 @@ size_t estimate_footprint(int n, long long nnz, const scgal_params& p) {
                    + 2.0 * 16.0 * n * p.R                        // reconstruction Y, U (FP64)
                    + 60.0 * p.T_max + 8.0 * 65 * 1216 + 65536    // history, q table, partials, scalars
                    + 8.0 * nnz + 24.0 * n;                       // sliced layout of the batched engine
+    return (size_t)(bytes * 1.15);
+}
+
+// Device bytes of one phase-retrieval solve (complex vectors; mirrors the
+// handle's allocations, with margin).
+size_t estimate_footprint_phase(int n, int L, const scgal_params& p) {
+    const double q = std::ceil(std::pow((double)p.T_max, 0.25) * std::log((double)n));
+    const double qmax = std::min<double>(q, n - 1);
+    const double ldb = (double)((n + 63) / 64 * 64);
+    const double vb = p.precision == 64 ? 16.0 : 8.0;   // complex element
+    const double d = (double)L * n;
+    double bytes = vb * (qmax + 1) * ldb                          // Lanczos basis
+                   + vb * (L + 2) * ldb                           // D x planes, v
+                   + (p.omega == SCGAL_OMEGA_REGEN ? 1.0 : 2.0) * vb * n * p.R   // S, and Omega unless regenerated
+                   + vb * (2.0 * d + n)                           // masks, FFT scratch, twiddles
+                   + 0.5 * vb * d + 24.0 * d                      // weights; z, y, b
+                   + 2.0 * 16.0 * n * p.R                         // reconstruction Y, U (complex FP64)
+                   + 60.0 * p.T_max + 8.0 * 65 * 4096 + 65536;    // history, q table, partials, scalars
     return (size_t)(bytes * 1.15);
 }
 
@@ -284,9 +305,12 @@ struct scgal_server {
             for (int i : fresh) {
                 Slot& s = slots[i];
                 s.req.t_admit = now_ms();
-                const int rc = scgal_create_maxcut(s.req.row_ptr.data(), s.req.col.data(),
-                                                   s.req.has_w ? s.req.w.data() : nullptr, s.req.n, s.req.nnz, 0.0,
-                                                   &s.req.prm, &s.h);
+                const int rc = (s.req.kind == 1)
+                                   ? scgal_create_phase(s.req.masks.data(), s.req.L, s.req.n, s.req.b.data(), 0.0,
+                                                        &s.req.prm, &s.h)
+                                   : scgal_create_maxcut(s.req.row_ptr.data(), s.req.col.data(),
+                                                         s.req.has_w ? s.req.w.data() : nullptr, s.req.n, s.req.nnz,
+                                                         0.0, &s.req.prm, &s.h);
                 if (rc) {
                     s.h = nullptr;
                     finish(s, rc, nullptr);
@@ -382,6 +406,38 @@ int scgal_submit(scgal_srv_t s, const int32_t* row_ptr, const int32_t* col, cons
         }
     }
     r.footprint = estimate_footprint(n, nnz, *params);
+    r.t_submit = now_ms();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stopping) return SCGAL_ESTATE;
+    if (s->queue.size() >= scgal_server::QUEUE_MAX) return SCGAL_EBUSY;
+    r.id = s->next_id++;
+    *ticket = r.id;
+    ++s->submitted;
+    s->queue.push_back(std::move(r));
+    s->cv_work.notify_one();
+    return SCGAL_OK;
+}
+
+int scgal_submit_phase(scgal_srv_t s, const double* masks, int32_t L, int32_t n, const double* b,
+                       const scgal_params* params, uint64_t* ticket) {
+    if (!s || !masks || !b || !params || !ticket || L < 1 || n < 16 || n > (1 << 20) || (n & (n - 1)))
+        return SCGAL_EINVAL;
+    if (params->T_max < 1 || params->R < 1 || params->R > SCGAL_RMAX || params->R > n) return SCGAL_EINVAL;
+    Request r;
+    r.kind = 1;
+    r.n = n;
+    r.L = L;
+    r.prm = *params;
+    const size_t d = (size_t)L * n;
+    r.masks.resize(2 * d);
+    r.b.resize(d);
+    // the caller's buffers may be host or device memory
+    if (cudaMemcpy(r.masks.data(), masks, sizeof(double) * 2 * d, cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(r.b.data(), b, sizeof(double) * d, cudaMemcpyDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return SCGAL_ECUDA;
+    }
+    r.footprint = estimate_footprint_phase(n, L, *params);
     r.t_submit = now_ms();
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stopping) return SCGAL_ESTATE;

@@ -103,6 +103,8 @@ _PROTOS = {
     "scgal_server_create": (c_int, [c_size_t, c_int32, POINTER(c_void_p)]),
     "scgal_submit": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int64, POINTER(scgal_params),
                              POINTER(c_uint64)]),
+    "scgal_submit_phase": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, POINTER(scgal_params),
+                                   POINTER(c_uint64)]),
     "scgal_poll": (c_int, [c_void_p, c_uint64, POINTER(scgal_result), c_int32]),
     "scgal_server_get_stats": (c_int, [c_void_p, POINTER(scgal_server_stats)]),
     "scgal_server_destroy": (c_int, [c_void_p]),
@@ -362,6 +364,17 @@ def scgal_submit(s: Server, row_ptr, col, w, n: int, nnz: int, params: scgal_par
     ticket = c_uint64(0)
     _check(load().scgal_submit(s.raw, _ptr(row_ptr), _ptr(col), _ptr(w), int(n), int(nnz), ctypes.byref(params),
                                ctypes.byref(ticket)), "scgal_submit")
+    return int(ticket.value)
+
+
+def scgal_submit_phase(s: Server, masks, L: int, n: int, b, params: scgal_params) -> int:
+    """masks: complex128[L, n] (or float64[L, n, 2]); b: float64[L * n]."""
+    m = masks
+    if isinstance(m, np.ndarray) and np.iscomplexobj(m):
+        m = np.ascontiguousarray(m.astype(np.complex128)).view(np.float64)
+    ticket = c_uint64(0)
+    _check(load().scgal_submit_phase(s.raw, _ptr(m), int(L), int(n), _ptr(b), ctypes.byref(params),
+                                     ctypes.byref(ticket)), "scgal_submit_phase")
     return int(ticket.value)
 
 

@@ -97,5 +97,8 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     good = S.scgal_params_default(R=2)
     for (M, N, s_) in ((6, 12, 3), (8, 12, 5), (16, 8, 2), (128, 256, 2), (1, 4, 2)):
         assert lib.scgal_create_ptycho(pp, M, N, s_, pp, 0.0, ctypes.byref(good), ctypes.byref(h)) == S.SCGAL_EINVAL
+    # a phase-retrieval submission without a server is rejected on the host
+    t = ctypes.c_uint64()
+    assert lib.scgal_submit_phase(None, pp, 1, 16, pp, ctypes.byref(good), ctypes.byref(t)) == S.SCGAL_EINVAL
     assert lib.scgal_strerror(S.SCGAL_ENUMERIC).decode() == "numerical failure"
     assert lib.scgal_step(None, None) == S.SCGAL_EINVAL

@@ -248,3 +248,34 @@ def test_batched_solve_converges_early():
     assert res["status"] == S.SCGAL_OK
     assert 1 <= res["iterations"] < 3000
     assert res["relgap"] <= 5e-2 and res["infeas"] <= 5e-2
+
+
+def test_served_phase_retrieval_equals_standalone():
+    """A coded-diffraction request served beside MaxCut requests runs on its own
+    graphs: its objective and infeasibility equal the standalone handle's bit
+    for bit, and the MaxCut requests of the same rounds are unaffected."""
+    from paper_1912_02949_gb300 import scgal as S
+    S.load()
+    n, L, T = 1024, 5, 40
+    pd = W.phase_problem(n, L, seed=0)
+    p = S.scgal_params_default(R=5, T_max=T, precision=32)
+    h = S.scgal_create_phase(pd.masks, L, n, pd.b, 0.0, p)
+    rc, last = S.scgal_solve(h, T)
+    _, lam, _, _ = S.scgal_reconstruct(h, want_cut=False)
+    h.close()
+    g = W.er_graph(2000, 8000, seed=3, weights="unit")
+    rp, col, _ = g.csr()
+    pm = S.scgal_params_default(R=10, T_max=30, precision=32)
+    alone = S.scgal_server_create(1 << 32, 4)
+    ref_mc = S.scgal_poll(alone, S.scgal_submit(alone, rp, col, None, g.n, col.size, pm), -1)
+    S.scgal_server_destroy(alone)
+    srv = S.scgal_server_create(1 << 32, 4)
+    t_mc = S.scgal_submit(srv, rp, col, None, g.n, col.size, pm)
+    t_ph = S.scgal_submit_phase(srv, pd.masks, L, n, pd.b, p)
+    res_ph = S.scgal_poll(srv, t_ph, -1)
+    res_mc = S.scgal_poll(srv, t_mc, -1)
+    S.scgal_server_destroy(srv)
+    assert res_ph["status"] == S.SCGAL_ENOTDONE and res_ph["iterations"] == T and res_ph["n"] == n
+    assert res_ph["objective"] == last["p"] and res_ph["infeas"] == last["infeas"]
+    assert res_ph["best_cut"] == 0 and abs(res_ph["lambda_max"] - lam[0]) <= 1e-6 * lam[0]
+    assert _result_fields(res_mc) == _result_fields(ref_mc)
