@@ -11,10 +11,11 @@
 // block and an arrival counter.  Here that scratch is a file-scope device array
 // that exists once per GPU for as long as the library stays loaded.
 //
-// The kernel is the Lanczos D-matvec step of the solver (one group of G lanes
-// per CSR row, G a power of two picked from the average degree), launched with
-// one block per 256/G rows, so the number of partial sums grows with n; the
-// array is sized for n <= 2^20 rows at any degree (8 rows per block at G = 32).
+// The kernel computes the same D-matvec as the solver's Lanczos step but is a
+// kernel of its own: one group of G lanes per CSR row (G the smallest power of
+// two >= the average degree, at most 32), launched with one block per 256/G
+// rows, so the number of partial sums grows with n; the array is sized for
+// n <= 2^20 rows at any degree (8 rows per block at G = 32).
 #include <mutex>
 
 #include "internal.h"
@@ -62,6 +63,31 @@ k_dmatvec_noalloc(const int* __restrict__ row_ptr, const int* __restrict__ col, 
 std::mutex g_setup_mu;
 double* g_scratch_ptr[64] = {nullptr};
 
+// Restores the caller's current device on every return path.
+struct CurrentDeviceRestore {
+    int prev = -1;
+    CurrentDeviceRestore() {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+    }
+    ~CurrentDeviceRestore() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// True when p is device (or managed) memory of device dev.
+bool on_device(const void* p, int dev) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return false;
+    return attr.device == dev;
+}
+
 }  // namespace
 
 extern "C" int scgal_dmatvec_noalloc(const int32_t* row_ptr, const int32_t* col, const float* val,
@@ -69,7 +95,7 @@ extern "C" int scgal_dmatvec_noalloc(const int32_t* row_ptr, const int32_t* col,
                                      float* y, double* dot, void* stream) {
     if (!row_ptr || !diag || !x || !y || !dot || (nnz > 0 && !col)) return SCGAL_EINVAL;
     if (n < 1 || n > kNoallocMaxRows || nnz < 0 || nnz >= (1ll << 31)) return SCGAL_EINVAL;
-    // the GPU that holds x is the one the kernel runs on
+    // the GPU that holds x is the one the kernel runs on; every other array must live there too
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, x) != cudaSuccess) {
         cudaGetLastError();
@@ -78,6 +104,10 @@ extern "C" int scgal_dmatvec_noalloc(const int32_t* row_ptr, const int32_t* col,
     if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) return SCGAL_EINVAL;
     const int dev = attr.device;
     if (dev < 0 || dev >= 64) return SCGAL_EINVAL;
+    if (!on_device(row_ptr, dev) || !on_device(diag, dev) || !on_device(y, dev) || !on_device(dot, dev) ||
+        (nnz > 0 && !on_device(col, dev)) || (val && nnz > 0 && !on_device(val, dev)))
+        return SCGAL_EINVAL;
+    CurrentDeviceRestore restore;
     if (cudaSetDevice(dev) != cudaSuccess) {
         cudaGetLastError();
         return SCGAL_ECUDA;
