@@ -59,6 +59,17 @@ enum { SCGAL_OMEGA_STORED = 0,  /* Omega drawn once (FP64 normals) and kept on t
                                     the sketch state halves).  FP64 solves give results
                                     identical to STORED; FP32 ones differ by rounding. */
 
+enum { SCGAL_SPMV_AUTO = 0,    /* MaxCut D-matvec kernel chosen by the library: TILED for FP32
+                                   handles whose graph suits it (65536 <= n <= 2^21, at least 24
+                                   stored entries per tile on average), else GATHER; with
+                                   tune = 1 both are timed at create and the faster kept */
+       SCGAL_SPMV_GATHER = 1,  /* CSR rows, a warp per 32 rows, x gathered from L2 */
+       SCGAL_SPMV_TILED = 2 }; /* 2-D tiles of 1024 rows x 16384 (FP32) or 8192 (FP64) columns:
+                                   pass 1 stages a column block of x in shared memory and writes
+                                   one product per stored entry, pass 2 adds each row's products
+                                   in shared memory; SCGAL_EINVAL if the graph does not fit the
+                                   tile encoding (n > 2^21 FP32 / 2^20 FP64, or n < 4) */
+
 enum { SCGAL_K_EQ = 0,    /* A(X) = b: the model problem (Eq. 2.2, Alg. 6.1) */
        SCGAL_K_LEQ = 1 };  /* A(X) <= b componentwise: the general template of App. D with
                               K = {u : u <= b} (App. D.3 item 1), through the slack
@@ -95,7 +106,11 @@ typedef struct {
                                candidates (2, 4, 6, 8 blocks per SM) on their own graph at
                                create, cached per (precision, weight kind, log2 n, log2 of
                                the average degree) in the process; results then differ from
-                               the fixed shape (6 blocks per SM, default 0) by rounding */
+                               the fixed shape (6 blocks per SM, default 0) by rounding.  With
+                               spmv = AUTO it also times the tiled kernels against the best
+                               gather grid and keeps the faster */
+    int32_t  spmv;          /* SCGAL_SPMV_*: MaxCut D-matvec kernel (default AUTO); ignored
+                               by the phase-retrieval problems */
 } scgal_params;
 
 /* One iteration record (Alg. 6.1 step t; stopping values of Eq. E.1 for the
@@ -125,6 +140,8 @@ typedef struct {
     int64_t device_bytes; /* device memory held by the handle */
     int32_t spmv_group;   /* lanes per CSR row chosen for the D-matvec */
     int32_t spmv_grid;    /* blocks of the MaxCut D-matvec grid (fixed or tuned); 0 otherwise */
+    int32_t spmv_kind;    /* MaxCut: SCGAL_SPMV_GATHER or SCGAL_SPMV_TILED in use; 0 otherwise */
+    int64_t tiled_slots;  /* MaxCut tiled layout: stored entries plus padding slots; 0 otherwise */
 } scgal_info;
 
 /* Fill *p with the defaults listed above. */
@@ -259,18 +276,23 @@ int scgal_time_kernel(scgal_t h, int32_t kernel, int32_t reps, double* ms_per_la
  * Computes, for a symmetric CSR graph with weights val (NULL = all 1),
  *     y[r] = diag[r] * x[r] + coff * sum_{j in row r} val[j] * x[col[j]]
  *     *dot = sum_r x[r] * y[r]      (FP64 sum in a fixed order: deterministic)
- * which is the D-matvec step of the solver's Lanczos loop (MaxCut: diag = the
- * diagonal of C' + A'*(w), coff = 1/(4 ||C||_F)).  All arrays are device memory
- * owned by the caller: row_ptr[n+1], col[nnz] (0 <= col < n, not checked),
- * val[nnz], diag[n], x[n], y[n] (written), dot (one double, written).  The work
- * runs on `stream` (a cudaStream_t; NULL = the legacy default stream) on the
- * GPU that holds x, and the call returns without waiting for it.
+ * which is the quantity of the D-matvec step of the solver's Lanczos loop
+ * (MaxCut: diag = the diagonal of C' + A'*(w), coff = 1/(4 ||C||_F)), computed
+ * by a kernel of its own (a group of G lanes per row, G the smallest power of
+ * two >= the average degree, at most 32), not by the solver's kernels.  All
+ * arrays are device memory owned by the caller, on one GPU: row_ptr[n+1],
+ * col[nnz] (0 <= col < n, not checked), val[nnz], diag[n], x[n], y[n]
+ * (written), dot (one double, written).  The work runs on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream) on the GPU that holds x, and
+ * the call returns without waiting for it; the caller's current device is the
+ * same after the call as before it.
  *
  * Scratch: the reduction's per-block partial sums and arrival counter live in
  * one static device array of 1 MB (plus 256 bytes) that every GPU which loads
  * the library keeps until the process exits.  It bounds the size:
  * n <= 1,048,576 rows (any degree); larger n, n < 1, a negative nnz, a NULL
- * array or x not in device memory return SCGAL_EINVAL before anything runs.
+ * array, or an array that is not device memory of the GPU holding x return
+ * SCGAL_EINVAL before anything runs.
  * The first call on each device looks up the array's device address (a one-time
  * set-up); make that first call before any stream capture.  All calls share the
  * array: calls that overlap on the GPU (on different streams, or from several

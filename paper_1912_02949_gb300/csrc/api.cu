@@ -153,7 +153,7 @@ int setup_state(scgal_ctx* h) {
     if (!h->c.omega_regen) ALLOC(h, om, sizeof(V) * (size_t)n * R);   // else regenerated at each use
     p.Omega = om;
     ALLOC(h, p.S, sizeof(V) * (size_t)n * R);
-    const int gmax = std::max(h->grid_elem, h->grid_spmv);
+    const int gmax = std::max(std::max(h->grid_elem, h->grid_spmv), p.tiled ? p.tNSG : 0);
     ALLOC(h, p.partials, sizeof(double) * (size_t)gmax * (1 + 2 * SCGAL_RMAX));
     ALLOC(h, p.ticket, sizeof(unsigned) * 4);
     ALLOC(h, p.sc, sizeof(DevScalars));
@@ -223,6 +223,7 @@ int check_params(const scgal_params* p) {
     if (p->omega != SCGAL_OMEGA_STORED && p->omega != SCGAL_OMEGA_REGEN) return SCGAL_EINVAL;
     if (p->kset != SCGAL_K_EQ && p->kset != SCGAL_K_LEQ) return SCGAL_EINVAL;
     if (p->tune != 0 && p->tune != 1) return SCGAL_EINVAL;
+    if (p->spmv != SCGAL_SPMV_AUTO && p->spmv != SCGAL_SPMV_GATHER && p->spmv != SCGAL_SPMV_TILED) return SCGAL_EINVAL;
     if (p->device >= 0) {
         int count = 0;
         if (cudaGetDeviceCount(&count) != cudaSuccess || p->device >= count) {
@@ -262,6 +263,65 @@ void delete_kp(scgal_ctx* h) {
 int copy_in(scgal_ctx* h, void* dst, const void* src, size_t bytes) {
     if (bytes == 0) return SCGAL_OK;
     CUDA_TRY(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->stream));
+    return SCGAL_OK;
+}
+
+// Tiled D-matvec layout (k_tiled.cu) built on the host from the packed CSR the
+// handle holds, then copied to the device.
+template <typename V>
+int tiled_setup(scgal_ctx* h, const TiledGeom& g) {
+    typedef typename VT<V>::R R;
+    KP<V>& p = kp<V>(h);
+    const int n = h->n;
+    const long long nnz = h->nnz;
+    cudaStream_t s = h->stream;
+    std::vector<int> rp((size_t)n + 1), cl((size_t)std::max<long long>(nnz, 1));
+    std::vector<R> vl;
+    CUDA_TRY(h, cudaMemcpyAsync(rp.data(), p.row_ptr, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
+    if (nnz > 0) CUDA_TRY(h, cudaMemcpyAsync(cl.data(), p.col, sizeof(int) * (size_t)nnz, cudaMemcpyDeviceToHost, s));
+    if (p.val) {
+        vl.resize((size_t)nnz);
+        CUDA_TRY(h, cudaMemcpyAsync(vl.data(), p.val, sizeof(R) * (size_t)nnz, cudaMemcpyDeviceToHost, s));
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    std::vector<uint32_t> tseg;
+    std::vector<uint16_t> c16, r16;
+    std::vector<R> tval;
+    if (tiled_build<R>(n, rp.data(), cl.data(), p.val ? vl.data() : nullptr, g, tseg, c16, r16, tval))
+        return set_err(h, SCGAL_EINVAL, "graph too large for the tiled layout");
+    const size_t slots = std::max<size_t>(c16.size(), 4);
+    uint32_t* d_tseg = nullptr;
+    uint16_t *d_c16 = nullptr, *d_r16 = nullptr;
+    R* d_tval = nullptr;
+    R* d_prod = nullptr;
+    ALLOC(h, d_tseg, sizeof(uint32_t) * tseg.size());
+    ALLOC(h, d_c16, sizeof(uint16_t) * slots);
+    ALLOC(h, d_r16, sizeof(uint16_t) * slots);
+    ALLOC(h, d_prod, sizeof(R) * slots);
+    if (p.val) ALLOC(h, d_tval, sizeof(R) * slots);
+    CUDA_TRY(h, cudaMemsetAsync(d_prod, 0, sizeof(R) * slots, s));
+    CUDA_TRY(h, cudaMemcpyAsync(d_tseg, tseg.data(), sizeof(uint32_t) * tseg.size(), cudaMemcpyHostToDevice, s));
+    if (!c16.empty()) {
+        CUDA_TRY(h, cudaMemcpyAsync(d_c16, c16.data(), sizeof(uint16_t) * c16.size(), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(h, cudaMemcpyAsync(d_r16, r16.data(), sizeof(uint16_t) * r16.size(), cudaMemcpyHostToDevice, s));
+        if (p.val) CUDA_TRY(h, cudaMemcpyAsync(d_tval, tval.data(), sizeof(R) * tval.size(), cudaMemcpyHostToDevice, s));
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    p.tiled = 1;
+    p.tCB = g.CB;
+    p.tSR = g.SR;
+    p.tNSG = g.NSG;
+    p.tNJ = g.NJ;
+    p.tW = g.W;
+    p.tS = g.S;
+    p.tseg = d_tseg;
+    p.tc16 = d_c16;
+    p.tr16 = d_r16;
+    p.tval = d_tval;
+    p.tprod = d_prod;
+    h->tiled_slots = (long long)c16.size();
+    h->tiled_on = 1;
+    if (prepare_tiled_kernels<V>(p)) return set_err(h, SCGAL_ECUDA, "CUDA error preparing the tiled kernels");
     return SCGAL_OK;
 }
 
@@ -384,6 +444,17 @@ int maxcut_build(scgal_ctx* h, const int32_t* row_ptr, const int32_t* col, const
     // with tuning on, the reduction partials are sized for the largest candidate grid
     h->grid_spmv = grid_for(n, SCGAL_BS, h->prm.tune ? TUNE_CAPS[TUNE_NCAPS - 1] : TUNE_DEFAULT_CAP);
     h->grid_elem = grid_for((n + 3) / 4, SCGAL_BS, 8);
+    // D-matvec kernel: the tiled layout where the graph suits it (or when asked for)
+    if (h->prm.spmv != SCGAL_SPMV_GATHER) {
+        TiledGeom tg;
+        const bool force = h->prm.spmv == SCGAL_SPMV_TILED;
+        if (tiled_geometry(n, nnz, h->prec, num_sms(), force, &tg)) {
+            const int trc = tiled_setup<V>(h, tg);
+            if (trc) return trc;
+        } else if (force) {
+            return set_err(h, SCGAL_EINVAL, "graph does not fit the tiled layout");
+        }
+    }
     const int src = setup_state<V>(h);
     if (src || !h->prm.tune) return src;
     return tune_spmv_grid<V>(h);
@@ -483,7 +554,9 @@ int phase_build(scgal_ctx* h, const double* masks, const double* b) {
 // the handle's stream for each candidate grid of TUNE_CAPS blocks per SM, on the
 // handle's own graph and start vector with private iteration scalars (the
 // solver state is not touched: the step also writes D W_0 and omega_0, which the
-// first iteration rewrites), and the fastest is kept.  Results are cached per
+// first iteration rewrites), and the fastest is kept; a handle with a tiled
+// layout and spmv = AUTO then times the two tiled passes against that grid and
+// keeps the faster of the two kernels.  Results are cached per
 // (precision, weight kind, log2 n, log2 of the average degree) for the life of
 // the process, so repeated solves of one workload search once.  The grid
 // decides which rows each block's partial sums cover, so two grids give
@@ -498,8 +571,13 @@ struct TuneKey {
         return ld < o.ld;
     }
 };
+// cached pick: the gather grid (blocks per SM) and whether the tiled kernels won
+struct TunePick {
+    int cap;
+    int tiled;
+};
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune_cache;
+std::map<TuneKey, TunePick> g_tune_cache;
 
 int ilog2_floor(long long v) {
     int r = 0;
@@ -513,17 +591,24 @@ int ilog2_floor(long long v) {
 template <typename V>
 int tune_spmv_grid(scgal_ctx* h) {
     const int n = h->n;
+    KP<V>& hp = kp<V>(h);
+    const bool can_tiled = hp.tiled && h->prm.spmv == SCGAL_SPMV_AUTO;
+    const bool keep_tiled = hp.tiled && h->prm.spmv == SCGAL_SPMV_TILED;
     const TuneKey key{h->prec, h->c.wkind, ilog2_floor(n), ilog2_floor(std::max<long long>(1, h->nnz / n))};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            h->grid_spmv = grid_for(n, SCGAL_BS, it->second);
+            h->grid_spmv = grid_for(n, SCGAL_BS, it->second.cap);
+            if (can_tiled) {
+                hp.tiled = it->second.tiled;
+                h->tiled_on = hp.tiled;
+            }
             return SCGAL_OK;
         }
     }
     cudaStream_t s = h->stream;
-    KP<V> q = kp<V>(h);
+    KP<V> q = hp;
     DevScalars* sc = nullptr;
     CUDA_TRY(h, cudaMallocAsync((void**)&sc, sizeof(DevScalars), s));
     CUDA_TRY(h, cudaMemsetAsync(sc, 0, sizeof(DevScalars), s));
@@ -534,31 +619,46 @@ int tune_spmv_grid(scgal_ctx* h) {
     int best_cap = TUNE_DEFAULT_CAP;
     float best_ms = 0.f;
     constexpr int REPS = 10;
-    for (int k = 0; k < TUNE_NCAPS; ++k) {
-        const int g = grid_for(n, SCGAL_BS, TUNE_CAPS[k]);
+    auto time_it = [&](int g, float* ms) -> bool {
         launch_spmv_step<V>(q, g, h->spmv_group, 0, s);   // warm-up
         cudaEventRecord(e0, s);
         for (int r = 0; r < REPS; ++r) launch_spmv_step<V>(q, g, h->spmv_group, 0, s);
         cudaEventRecord(e1, s);
+        *ms = 0.f;
+        return cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(ms, e0, e1) == cudaSuccess;
+    };
+    bool ok = true;
+    q.tiled = 0;
+    for (int k = 0; k < TUNE_NCAPS && ok; ++k) {
         float ms = 0.f;
-        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            cudaFreeAsync(sc, s);
-            return set_err(h, SCGAL_ECUDA, "CUDA error while tuning the D-matvec");
-        }
+        ok = time_it(grid_for(n, SCGAL_BS, TUNE_CAPS[k]), &ms);
         if (k == 0 || ms < best_ms) {
             best_ms = ms;
             best_cap = TUNE_CAPS[k];
         }
     }
+    int tiled_pick = keep_tiled ? 1 : 0;
+    if (ok && can_tiled) {
+        float ms = 0.f;
+        q.tiled = 1;
+        ok = time_it(h->grid_spmv, &ms);
+        tiled_pick = ms < best_ms ? 1 : 0;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (!ok) {
+        cudaFreeAsync(sc, s);
+        return set_err(h, SCGAL_ECUDA, "CUDA error while tuning the D-matvec");
+    }
     CUDA_TRY(h, cudaFreeAsync(sc, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
     h->grid_spmv = grid_for(n, SCGAL_BS, best_cap);
+    if (can_tiled) {
+        hp.tiled = tiled_pick;
+        h->tiled_on = tiled_pick;
+    }
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = best_cap;
+    g_tune_cache[key] = TunePick{best_cap, tiled_pick};
     return SCGAL_OK;
 }
 
@@ -815,12 +915,18 @@ int do_reconstruct(scgal_ctx* h, double* U, double* lambda, double* err, int64_t
 }
 
 // scratch for apply_D / lanczos (allocated on first use)
+// Every part starts on a 256-byte boundary: the tiled D-matvec reads x with
+// bulk copies and 16-byte vector loads.
+constexpr size_t AUX_ALIGN = 256;
+inline size_t aux_round(size_t b) { return (b + AUX_ALIGN - 1) / AUX_ALIGN * AUX_ALIGN; }
+
 template <typename V>
 int ensure_aux(scgal_ctx* h) {
     if (h->aux) return SCGAL_OK;
     const size_t nv = (size_t)h->n * (h->cplx ? 2 : 1);
-    ALLOC(h, h->aux, sizeof(double) * (nv * 2 + (size_t)h->d) + sizeof(V) * (size_t)h->n * 2 +
-                         sizeof(typename VT<V>::R) * (size_t)h->d + sizeof(DevScalars) + sizeof(scgal_stats) + 256);
+    ALLOC(h, h->aux, aux_round(sizeof(double) * nv) * 2 + aux_round(sizeof(double) * (size_t)h->d) +
+                         aux_round(sizeof(V) * (size_t)h->n) * 2 + aux_round(sizeof(typename VT<V>::R) * (size_t)h->d) +
+                         aux_round(sizeof(DevScalars)) + sizeof(scgal_stats) + AUX_ALIGN);
     return SCGAL_OK;
 }
 
@@ -839,19 +945,23 @@ template <typename V>
 AuxView aux_view(scgal_ctx* h) {
     typedef typename VT<V>::R R;
     const size_t nv = (size_t)h->n * (h->cplx ? 2 : 1);
-    char* b = reinterpret_cast<char*>(h->aux);
+    char* q = reinterpret_cast<char*>(h->aux);
     AuxView a;
-    a.xd = reinterpret_cast<double*>(b);
-    a.outd = a.xd + nv;
-    a.wd = a.outd + nv;
-    char* q = reinterpret_cast<char*>(a.wd + h->d);
+    a.xd = reinterpret_cast<double*>(q);
+    q += aux_round(sizeof(double) * nv);
+    a.outd = reinterpret_cast<double*>(q);
+    q += aux_round(sizeof(double) * nv);
+    a.wd = reinterpret_cast<double*>(q);
+    q += aux_round(sizeof(double) * (size_t)h->d);
     a.xv = q;
-    a.outv = q + sizeof(V) * (size_t)h->n;
-    a.wv = q + sizeof(V) * (size_t)h->n * 2;
-    q += sizeof(V) * (size_t)h->n * 2 + sizeof(R) * (size_t)h->d;
-    q = reinterpret_cast<char*>(((uintptr_t)q + 15) & ~(uintptr_t)15);
+    q += aux_round(sizeof(V) * (size_t)h->n);
+    a.outv = q;
+    q += aux_round(sizeof(V) * (size_t)h->n);
+    a.wv = q;
+    q += aux_round(sizeof(R) * (size_t)h->d);
     a.sc = reinterpret_cast<DevScalars*>(q);
-    a.hist = reinterpret_cast<scgal_stats*>(q + sizeof(DevScalars));
+    q += aux_round(sizeof(DevScalars));
+    a.hist = reinterpret_cast<scgal_stats*>(q);
     return a;
 }
 
@@ -1460,6 +1570,10 @@ int scgal_get_info(scgal_t h, scgal_info* out) {
     out->device_bytes = h->device_bytes;
     out->spmv_group = h->spmv_group;
     out->spmv_grid = h->kind == KIND_MAXCUT ? h->grid_spmv : 0;
+    if (h->kind == KIND_MAXCUT) {
+        out->spmv_kind = h->tiled_on ? SCGAL_SPMV_TILED : SCGAL_SPMV_GATHER;
+        out->tiled_slots = h->tiled_on ? h->tiled_slots : 0;
+    }
     return SCGAL_OK;
 }
 

@@ -112,18 +112,27 @@ struct KP {
     double* upart;      // per-block partial ||W_{i+1}||^2 of the last Lanczos update
     int nupd;           // blocks of the Lanczos update kernel (entries of upart)
     const int* qtab;    // q_t for t = 1..T_max (computed on the host)
+    // tiled MaxCut D-matvec (k_tiled.cu): tiles (J, SG) of tSR rows x tCB columns,
+    // stored column-block-major (tile J * tNSG + SG); every slot holds one stored
+    // entry (or padding) of the CSR
+    int tiled;          // 1: the D-matvec runs on the tiled layout
+    int tCB, tSR, tNSG, tNJ, tW, tS;   // block sizes, tile counts, warps of pass 2, CTAs per column block of pass 1
+    const uint32_t* tseg;              // tNJ * tNSG + 1 slot offsets
+    const uint16_t* tc16;              // column within the column block | sign of the weight << 15
+    const uint16_t* tr16;              // row within the super-group | run flags (k_tiled.cu)
+    const typename VT<V>::R* tval;     // per-slot weight (general weights only)
+    typename VT<V>::R* tprod;          // per-slot products of the current D-matvec
 };
 
-// Last block of a Lanczos D-matvec step i (all threads of the block call it):
-// rho_{i-1} from the previous update's per-block partials, the breakdown test
-// of Alg. 4.1 (exact rho == 0), the scale s_i = 1 / rho_{i-1}, and
-// omega_i = s_i^2 <W_i, D W_i>.  Nothing is recorded once the iteration has
-// converged or broken down.
+// End of a Lanczos D-matvec step i, thread 0 of the last block only: from
+// rr = ||W_i||^2 (the previous update's per-block partials, summed) rho_{i-1},
+// the breakdown test of Alg. 4.1 (exact rho == 0), the scale s_i = 1 / rho_{i-1},
+// and omega_i = s_i^2 <W_i, D W_i> from dot = <W_i, D W_i>.  Nothing is recorded
+// once the iteration has converged or broken down.
 template <typename V>
-__device__ __forceinline__ void finish_lanczos_step(const KP<V>& p, int i, double dot) {
+__device__ __forceinline__ void finish_lanczos_scalars(const KP<V>& p, int i, double dot, double rr) {
     DevScalars* sc = p.sc;
-    const double rr = (i > 0) ? block_sum_array(p.upart, p.nupd) : 0.0;
-    if (threadIdx.x != 0 || sc->converged || sc->stop) return;
+    if (sc->converged || sc->stop) return;
     if (i > 0) {
         const double rho = sqrt(rr);
         if (rho == 0.0) {           // invariant subspace found: T is i x i
@@ -149,6 +158,13 @@ __device__ __forceinline__ void finish_lanczos_step(const KP<V>& p, int i, doubl
     sc->k = i + 1;
 }
 
+// The same for a last block of SCGAL_BS threads (all of them call it).
+template <typename V>
+__device__ __forceinline__ void finish_lanczos_step(const KP<V>& p, int i, double dot) {
+    const double rr = (i > 0) ? block_sum_array(p.upart, p.nupd) : 0.0;
+    if (threadIdx.x == 0) finish_lanczos_scalars(p, i, dot, rr);
+}
+
 }  // namespace scgal
 
 // ---------------------------------------------------------------------------
@@ -165,6 +181,8 @@ struct scgal_ctx {
     double alpha_orig = 0, normC = 0, normA = 0;
     int trace_correct = 1;
     int spmv_group = 8;
+    long long tiled_slots = 0;  // slots of the tiled layout (0: none built)
+    int tiled_on = 0;           // the iteration graphs use the tiled D-matvec
     int grid_elem = 1, grid_spmv = 1, grid_ritz = 1;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream the iteration graphs are captured on
@@ -227,6 +245,19 @@ template <typename V>
 int nystrom_reconstruct(const V* S, const V* Om, int n, int R, double tau, int trace_correct, double alpha,
                         double2* part, int grid, double2* G, double2* L, double2* M, double* scal,
                         typename VT<V>::D* Y, typename VT<V>::D* U, double* lam, double* err, cudaStream_t s);
+
+// MaxCut tiled D-matvec (k_tiled.cu)
+struct TiledGeom {
+    int CB, SR, NSG, NJ, W, S;
+};
+int tiled_geometry(int n, long long nnz, int prec, int sms, bool force, TiledGeom* g);
+template <typename R>
+int tiled_build(int n, const int* row_ptr, const int* col, const R* val, const TiledGeom& g,
+                std::vector<uint32_t>& tseg, std::vector<uint16_t>& c16, std::vector<uint16_t>& r16,
+                std::vector<R>& tval);
+template <typename V> int prepare_tiled_kernels(const KP<V>& p);
+template <typename V> void launch_tiled_step(const KP<V>& p, int i, cudaStream_t s);
+template <typename V> void launch_tiled_apply(const KP<V>& p, const V* x, V* out, const V* diag, cudaStream_t s);
 
 // MaxCut
 template <typename V> void launch_spmv_step(const KP<V>& p, int grid, int group, int i, cudaStream_t s);

@@ -3,7 +3,9 @@
 // D-matvec.  D = C' + A'*(w) with C' = -sC L / 4 and A'* w = sA diag(w), so
 //     (D x)_r = dvec_r x_r + coff * sum_{j in N(r)} w_rj x_j,
 //     dvec_r  = -sC deg_r / 4 + sA w_r,     coff = sC / 4,
-// one CSR pass, a warp per chunk of 32 rows (spmv_chunks).
+// one CSR pass, a warp per chunk of 32 rows (spmv_chunks), or, for handles on
+// the tiled layout, the two passes of k_tiled.cu (the v* C v pass of the z
+// update always runs here).
 // Weights: unit (no value array), +/-1 (sign packed in bit 31 of the column
 // index: 4 bytes per stored entry), or general (value array).
 #include <algorithm>
@@ -260,7 +262,8 @@ static void spmv_dispatch(const KP<V>& p, int grid, int group, cudaStream_t s, i
 }
 
 template <typename V> void launch_spmv_step(const KP<V>& p, int grid, int group, int i, cudaStream_t s) {
-    spmv_dispatch<V>(p, grid, group, s, 0, i);
+    if (p.tiled) launch_tiled_step<V>(p, i, s);
+    else spmv_dispatch<V>(p, grid, group, s, 0, i);
 }
 template <typename V> void launch_vcv_update(const KP<V>& p, int grid, int group, cudaStream_t s) {
     spmv_dispatch<V>(p, grid, group, s, 1, 0);
@@ -268,7 +271,8 @@ template <typename V> void launch_vcv_update(const KP<V>& p, int grid, int group
 template <typename V>
 void launch_apply_D_maxcut(const KP<V>& p, int grid, int group, const V* x, V* out, const V* diag,
                            cudaStream_t s) {
-    spmv_dispatch<V>(p, grid, group, s, 2, 0, x, out, diag);
+    if (p.tiled) launch_tiled_apply<V>(p, x, out, diag, s);
+    else spmv_dispatch<V>(p, grid, group, s, 2, 0, x, out, diag);
 }
 template <typename V> void launch_dvec_from_w(const KP<V>& p, int grid, const double* w, cudaStream_t s) {
     k_dvec_from_w<V><<<grid, SCGAL_BS, 0, s>>>(p, w);
