@@ -162,7 +162,8 @@ int setup_state(scgal_ctx* h) {
     ALLOC(h, p.sv, sizeof(double) * (h->qmax + 2));
     ALLOC(h, p.coef, sizeof(double) * (h->qmax + 2));
     ALLOC(h, p.hist, sizeof(scgal_stats) * (size_t)hist_cap);
-    ALLOC(h, p.upart, sizeof(double) * (size_t)gmax);
+    p.nupd = update_grid<V>(n);   // blocks of every Lanczos update launch (one partial each)
+    ALLOC(h, p.upart, sizeof(double) * (size_t)std::max(gmax, p.nupd));
     {
         int* qt = nullptr;
         ALLOC(h, qt, sizeof(int) * (size_t)h->prm.T_max);
@@ -188,7 +189,6 @@ int setup_state(scgal_ctx* h) {
     prepare_lanczos_shapes<V>();
     if constexpr (!VT<V>::cplx) prepare_maxcut_shapes<V>();
     h->grid_ritz = std::min(h->grid_elem, ritz_resident<V>(p));
-    p.nupd = update_grid<V>(h->grid_elem);   // blocks of every Lanczos update launch
     if (!h->c.omega_regen) launch_gen_omega<V>(p, grid_for((long long)n * R, SCGAL_BS, 8), s);
     launch_dual_start<V>(p, h->grid_elem, 0, s);
     CUDA_TRY(h, cudaGetLastError());

@@ -192,6 +192,33 @@ __device__ __forceinline__ void omega_row(unsigned long long seed, unsigned inst
 }
 
 // --------------------------------------------------------------------------
+// Per-thread sum of products x*y for the FP64 reductions: FP64 in the FP64
+// path; in the FP32 path each product is split exactly by one FMA (x y = p + pe)
+// and the running sum is carried exactly by the two-sum rule (s + p = t + te),
+// so a thread's partial is exact up to the final float pair; total() hands it
+// to the FP64 sums across threads.  The intrinsics keep the compiler from
+// fusing or reordering these operations.
+template <typename R> struct CompSum;
+template <> struct CompSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x, double y) { s = fma(x, y, s); }
+    __device__ __forceinline__ double total() const { return s; }
+};
+template <> struct CompSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x, float y) {
+        const float p = __fmul_rn(x, y);
+        const float pe = fmaf(x, y, -p);
+        const float t = __fadd_rn(s, p);
+        const float bb = __fsub_rn(t, s);
+        const float te = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(te, pe));
+    }
+    __device__ __forceinline__ double total() const { return (double)s + (double)c; }
+};
+
+// --------------------------------------------------------------------------
 // Deterministic grid reduction of NV doubles (blockDim.x == SCGAL_BS; 1-D or
 // 2-D grids, blocks numbered blockIdx.y * gridDim.x + blockIdx.x).
 // Returns true in exactly one block (the last to arrive); there tot[0..NV)

@@ -227,7 +227,7 @@ template <typename V> void launch_regen_omega(const KP<V>& p, V* out, cudaStream
 template <typename V> void launch_start_only(const KP<V>& p, int grid, long long t, cudaStream_t s);
 // launch-shape queries (call before any stream capture)
 template <typename V> int ritz_resident(const KP<V>& p);
-template <typename V> int update_grid(int grid);
+template <typename V> int update_grid(long long n);
 template <typename V> void prepare_lanczos_shapes();
 template <typename V> void prepare_maxcut_shapes();
 

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_dual_start(KP<V> p, int do_dual) {
     const double beta1 = p.c.beta0 * sqrt((double)(t1 + 1));
     const int n = p.c.n, d = p.c.d;
     double a_yb = 0.0, a_zz = 0.0, a_nzb = 0.0;
-    Rt a_w0 = 0;
+    CompSum<Rt> a_w0;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
     for (int i = gt; i < d; i += st) {
         const double bi = p.c.b_const ? p.c.bconst : p.b[i];
@@ -70,21 +70,22 @@ __global__ void __launch_bounds__(SCGAL_BS) k_dual_start(KP<V> p, int do_dual) {
             v.x = n0;
             v.y = n1;
             p.basis[e] = v;
-            a_w0 += n0 * n0 + n1 * n1;
+            a_w0.add(n0, n0);
+            a_w0.add(n1, n1);
         }
     } else {
         for (int pr = gt; 2 * pr < n; pr += st) {
             Rt n0, n1;
             normal_pair(p.c.seed, PURPOSE_LANCZOS, tt, p.c.instance, (unsigned)pr, n0, n1);
             p.basis[2 * pr] = n0;
-            a_w0 += n0 * n0;
+            a_w0.add(n0, n0);
             if (2 * pr + 1 < n) {
                 p.basis[2 * pr + 1] = n1;
-                a_w0 += n1 * n1;
+                a_w0.add(n1, n1);
             }
         }
     }
-    double v[4] = {a_yb, a_zz, a_nzb, (double)a_w0};
+    double v[4] = {a_yb, a_zz, a_nzb, a_w0.total()};
     __shared__ double tot[4];
     if (grid_reduce<4>(v, p.partials, p.ticket, tot)) {
         if (threadIdx.x == 0) {
@@ -109,9 +110,10 @@ __global__ void __launch_bounds__(SCGAL_BS) k_dual_start(KP<V> p, int do_dual) {
 // D-matvec step adds them up (finish_lanczos_step).  Speculative like that step:
 // after a breakdown sv[i] may be stale, and the row it writes is never read.
 template <typename V>
-__global__ void __launch_bounds__(SCGAL_BS, 8) k_lanczos_update(KP<V> p, int i) {
+__global__ void __launch_bounds__(SCGAL_BS, 4) k_lanczos_update(KP<V> p, int i) {
     typedef typename VT<V>::R Rt;
     constexpr int W = 16 / sizeof(Rt);
+    constexpr int UN = 2;              // 16-byte groups per thread in flight
     struct alignas(16) RV { Rt v[W]; };
     pdl_wait();
     const double si = p.sv[i];
@@ -127,33 +129,46 @@ __global__ void __launch_bounds__(SCGAL_BS, 8) k_lanczos_update(KP<V> p, int i) 
     Rt* __restrict__ Wn = reinterpret_cast<Rt*>(p.basis) + (size_t)(i + 1) * ldr;
     const int np = p.ynplanes;
     const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
-    Rt acc = 0;
+    CompSum<Rt> acc;
     const long long mv = m / W;
-    for (long long k = gt; k < mv; k += st) {
-        RV y = reinterpret_cast<const RV*>(Y)[k];
-        for (int g = 1; g < np; ++g) {
-            const RV yg = reinterpret_cast<const RV*>(Y + (size_t)g * ldr)[k];
+    for (long long k0 = gt; k0 < mv; k0 += st * UN) {
+        RV y[UN], wi[UN], wm[UN];
 #pragma unroll
-            for (int j = 0; j < W; ++j) y.v[j] += yg.v[j];
+        for (int u = 0; u < UN; ++u) {
+            const long long k = k0 + u * st;
+            if (k < mv) {
+                y[u] = reinterpret_cast<const RV*>(Y)[k];
+                wi[u] = reinterpret_cast<const RV*>(Wi)[k];
+                wm[u] = reinterpret_cast<const RV*>(Wm)[k];
+            }
         }
-        const RV wi = reinterpret_cast<const RV*>(Wi)[k];
-        const RV wm = reinterpret_cast<const RV*>(Wm)[k];
-        RV wn;
 #pragma unroll
-        for (int j = 0; j < W; ++j) {
-            wn.v[j] = lin3(a, y.v[j], b, wi.v[j], c, wm.v[j]);
-            acc += wn.v[j] * wn.v[j];
+        for (int u = 0; u < UN; ++u) {
+            const long long k = k0 + u * st;
+            if (k < mv) {
+                for (int g = 1; g < np; ++g) {
+                    const RV yg = reinterpret_cast<const RV*>(Y + (size_t)g * ldr)[k];
+#pragma unroll
+                    for (int j = 0; j < W; ++j) y[u].v[j] += yg.v[j];
+                }
+                RV wn;
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    wn.v[j] = lin3(a, y[u].v[j], b, wi[u].v[j], c, wm[u].v[j]);
+                    acc.add(wn.v[j], wn.v[j]);
+                }
+                reinterpret_cast<RV*>(Wn)[k] = wn;
+            }
         }
-        reinterpret_cast<RV*>(Wn)[k] = wn;
     }
     for (long long k = mv * W + gt; k < m; k += st) {   // tail
         Rt y = Y[k];
         for (int g = 1; g < np; ++g) y += Y[(size_t)g * ldr + k];
         const Rt w = lin3(a, y, b, Wi[k], c, Wm[k]);
         Wn[k] = w;
-        acc += w * w;
+        acc.add(w, w);
     }
-    block_sum_to<Rt>(acc, p.upart + blockIdx.x);
+    block_sum_to<double>(acc.total(), p.upart + blockIdx.x);
 }
 
 template <typename V>
@@ -389,7 +404,14 @@ template <typename V> void prepare_lanczos_shapes() {
 template <typename V> void launch_dual_start(const KP<V>& p, int grid, int do_dual, cudaStream_t s) {
     launch_pdl(k_dual_start<V>, std::min(grid, resident_dual<V>()), SCGAL_BS, 0, s, p, do_dual);
 }
-template <typename V> int update_grid(int grid) { return std::min(grid, resident_update<V>()); }
+// Blocks of the update: enough for one round of two 16-byte groups per thread,
+// within one wave.
+template <typename V> int update_grid(long long n) {
+    constexpr int CF = VT<V>::cplx ? 2 : 1;
+    const long long groups = (n * CF * (long long)sizeof(typename VT<V>::R) + 15) / 16;
+    const long long want = (groups + 2LL * SCGAL_BS - 1) / (2LL * SCGAL_BS);
+    return (int)std::max<long long>(1, std::min<long long>(want, resident_update<V>()));
+}
 template <typename V> void launch_lanczos_update(const KP<V>& p, int grid, int i, cudaStream_t s) {
     // the grid must be the one p.nupd was sized for: the next step reads nupd partials
     (void)grid;
@@ -426,7 +448,7 @@ template <typename V> void launch_regen_omega(const KP<V>& p, V* out, cudaStream
     template void launch_regen_omega<V>(const KP<V>&, V*, cudaStream_t);             \
     template void launch_start_only<V>(const KP<V>&, int, long long, cudaStream_t);  \
     template int ritz_resident<V>(const KP<V>&);                                      \
-    template int update_grid<V>(int);                                                  \
+    template int update_grid<V>(long long);                                            \
     template void prepare_lanczos_shapes<V>();
 INST(float)
 INST(double)

@@ -21,8 +21,8 @@ namespace scgal {
 // up its own row.  Three dependent memory round trips per 32 rows instead of per
 // row.  Chunks with more nonzeros than the per-warp buffer are done in pieces.
 template <typename V, int WK>
-__device__ __forceinline__ V spmv_chunks(const KP<V>& p, const V* __restrict__ x, V* __restrict__ out,
-                                         const V* __restrict__ diag) {
+__device__ __forceinline__ double spmv_chunks(const KP<V>& p, const V* __restrict__ x, V* __restrict__ out,
+                                              const V* __restrict__ diag) {
     constexpr int WPB = SCGAL_BS / 32;
     constexpr int CAP = 24576 / (WPB * (int)sizeof(V));   // products per warp per piece
     constexpr int U = 6;                                   // passes of 32 issued back to back
@@ -33,7 +33,7 @@ __device__ __forceinline__ V spmv_chunks(const KP<V>& p, const V* __restrict__ x
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const V coff = (V)p.c.coff;
-    V dot = 0;
+    CompSum<V> dot;
     long long r0 = warp * 32;
     // row data of the first chunk; later chunks are prefetched one chunk ahead.
     // The row pointers are static, so they are read before waiting for the
@@ -106,14 +106,14 @@ __device__ __forceinline__ V spmv_chunks(const KP<V>& p, const V* __restrict__ x
         if (act) {
             const V yr = fma(dr, xr, coff * acc);
             if (out) out[r] = yr;
-            dot = fma(xr, yr, dot);
+            dot.add(xr, yr);
         }
         rs = rs_n;
         re = re_n;
         xr = xr_n;
         dr = dr_n;
     }
-    return dot;
+    return dot.total();
 }
 
 // Lanczos step i: Y = D W_i and omega_i = s_i^2 <W_i, Y>.
@@ -123,10 +123,9 @@ __device__ __forceinline__ V spmv_chunks(const KP<V>& p, const V* __restrict__ x
 template <typename V, int WK>
 __global__ void __launch_bounds__(SCGAL_BS) k_spmv_step(KP<V> p, int i) {
     const V* x = p.basis + (size_t)i * p.ldb;
-    const V dot = spmv_chunks<V, WK>(p, x, p.ybuf, p.dvec);
-    V v[1] = {dot};
+    double v[1] = {spmv_chunks<V, WK>(p, x, p.ybuf, p.dvec)};
     __shared__ double tot[1];
-    if (grid_reduce<1, V>(v, p.partials, p.ticket, tot)) finish_lanczos_step(p, i, tot[0]);
+    if (grid_reduce<1, double>(v, p.partials, p.ticket, tot)) finish_lanczos_step(p, i, tot[0]);
 }
 
 // After the Ritz vector: v* C v (primitive (1), one more CSR pass), the primal
@@ -140,7 +139,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_vcv_update(KP<V> p) {
     pdl_wait();
     if (sc->converged) return;
     const V* __restrict__ v = p.vbuf;
-    const V vcv = spmv_chunks<V, WK>(p, v, nullptr, p.cdiag);
+    const double vcv = spmv_chunks<V, WK>(p, v, nullptr, p.cdiag);
     const double eta = sc->eta, nv2 = sc->nv2;
     const int take = sc->take_h;
     const int n = p.c.n, R = p.c.R;
@@ -187,7 +186,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_vcv_update(KP<V> p) {
         const int c = (int)(kk - (long long)e * R);
         p.S[kk] = fma(om1, p.S[kk], sfac * v[e] * rr[c]);
     }
-    double red[4] = {(double)vcv, a_nzb, a_yzb, a_yy};
+    double red[4] = {vcv, a_nzb, a_yzb, a_yy};
     __shared__ double tot[4];
     if (grid_reduce<4, double>(red, p.partials, p.ticket, tot)) {
         if (threadIdx.x == 0) {

@@ -103,27 +103,6 @@ __device__ __forceinline__ double flip_sign(double a, unsigned c) {
     return __longlong_as_double(__double_as_longlong(a) ^ ((long long)(c & 0x8000u) << 48));
 }
 
-// <x, y> accumulator of one lane: FP64, or (FP32 path) an exact float pair.
-template <typename R> struct DotAcc;
-template <> struct DotAcc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double x, double y) { s = fma(x, y, s); }
-    __device__ __forceinline__ double total() const { return s; }
-};
-template <> struct DotAcc<float> {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x, float y) {
-        const float p = __fmul_rn(x, y);
-        const float pe = fmaf(x, y, -p);              // x y = p + pe exactly
-        const float t = __fadd_rn(s, p);              // two-sum: s + p = t + te exactly
-        const float bb = __fsub_rn(t, s);
-        const float te = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
-        s = t;
-        c = __fadd_rn(c, __fadd_rn(te, pe));
-    }
-    __device__ __forceinline__ double total() const { return (double)s + (double)c; }
-};
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -219,8 +198,9 @@ __global__ void __launch_bounds__(TP_BS) k_tile_products(KP<V> p, const V* __res
 // ---------------------------------------------------------------------------
 // Pass 2: rows of super-group SG.  STEP: the Lanczos step i (x = W_i, out =
 // ybuf, diag = dvec, <x, D x> reduced and the step finished in the last block).
+// Seven 4-warp CTAs fit an SM, so the 1024 super-groups of n = 2^20 run in one wave.
 template <typename V, int W, bool STEP>
-__global__ void __launch_bounds__(W * 32) k_tile_rows(KP<V> p, int i, const V* __restrict__ x, V* __restrict__ out,
+__global__ void __launch_bounds__(W * 32, W == 4 ? 7 : 4) k_tile_rows(KP<V> p, int i, const V* __restrict__ x, V* __restrict__ out,
                                                       const V* __restrict__ diag) {
     typedef typename VT<V>::R R;
     extern __shared__ __align__(16) unsigned char tsm[];
@@ -309,7 +289,7 @@ __global__ void __launch_bounds__(W * 32) k_tile_rows(KP<V> p, int i, const V* _
     // rows of the super-group, four per lane per round; accumulators added in warp order
     const int n = p.c.n;
     const R coff = (R)p.c.coff;
-    DotAcc<R> dacc;
+    CompSum<R> dacc;
     const int rb = SG * SR;
     // four rows at a time through 16-byte accesses when x, diag and out allow them
     const bool vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(diag) |

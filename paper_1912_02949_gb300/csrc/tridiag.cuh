@@ -13,14 +13,16 @@ namespace scgal {
 //  1. Bracket: Sturm-count multisection in FP32 (each of the 256 threads counts
 //     the eigenvalues below one of 256 points; every round narrows the bracket
 //     257-fold), from the Gershgorin interval to FP32 resolution.
-//  2. FP32 path: inverse iteration in FP32 on T - sigma I with sigma below the
-//     bracket (positive definite, so elimination without pivoting is stable),
-//     and xi = the Rayleigh quotient of that vector in FP64.
-//     FP64 path: Laguerre's iteration on the characteristic polynomial p_k(x)
+//  2. The eigenpair in FP64, in both precisions: FP64 inverse iteration on
+//     T - sigma I with sigma below the smallest eigenvalue -- factored once
+//     (positive definite there, so elimination without pivoting is stable) and
+//     solved three times.  FP64 path: sigma just below the root found by
+//     Laguerre's iteration in FP64 on the characteristic polynomial p_k(x)
 //     (three-term recurrences for p, p', p'', rescaled by powers of two against
 //     overflow) from left of the bracket -- monotone and cubic to the smallest
-//     root of a real-rooted polynomial, clusters included -- then FP64 inverse
-//     iteration just below the root.
+//     root of a real-rooted polynomial, clusters included -- and xi = that root.
+//     FP32 path: sigma just below the FP32 bracket, and xi = the FP64 Rayleigh
+//     quotient of the FP64 eigenvector (its error is quadratic in the vector's).
 // The FP64 work is a few sequential passes over k: GB300's FP64 rate is low,
 // and a 256-thread FP64 bisection saturated the SM's FP64 pipe for ~1 ms.
 // Then the stopping values of Eq. E.1 for the state of iteration t (before its
@@ -113,116 +115,103 @@ __device__ void tridiag_body(const KP<V>& p, int q, double* smt) {
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            if constexpr (sizeof(typename VT<V>::R) == 4) {
-                // FP32 path: FP32 inverse iteration from below the bracket, then the
-                // Rayleigh quotient in FP64 (error quadratic in the vector's)
-                const float sigma = (float)s_lo - 2.0f * (float)(s_hi - s_lo) - 64.0f * FLT_EPSILON;
-                float* uf = reinterpret_cast<float*>(u);
-                float* mf = reinterpret_cast<float*>(m);
-                for (int i = 0; i < k; ++i) uf[i] = 1.0f;
-                for (int it = 0; it < 3; ++it) {
-                    float mm = af[0] - sigma;
-                    if (fabsf(mm) < 1e-30f) mm = 1e-30f;
-                    mf[0] = mm;
+            constexpr bool LAGUERRE = sizeof(typename VT<V>::R) == 8;
+            double sigma;
+            if constexpr (LAGUERRE) {
+                // FP64 path: Laguerre's iteration on p_k(x) of the scaled matrix, from
+                // left of the bracket (cubic, and monotone to the smallest root even
+                // through clusters); eigenvalues of the scaled matrix are accurate to
+                // ~eps in absolute terms, so the stopping test is absolute
+                const double margin = 256.0 * FLT_EPSILON;
+                const double kk = (double)k;
+                double x = s_lo - margin;
+                for (int it = 0; it < 40; ++it) {
+                    double p0 = 1.0, p1 = a[0] - x;               // p_0, p_1
+                    double d0 = 0.0, d1 = -1.0;                   // first derivatives
+                    double h0 = 0.0, h1 = 0.0;                    // second derivatives
                     for (int i = 1; i < k; ++i) {
-                        const float es = (float)e[i - 1];
-                        const float l = es / mf[i - 1];
-                        mm = (af[i] - sigma) - l * es;
-                        if (fabsf(mm) < 1e-30f) mm = 1e-30f;
-                        mf[i] = mm;
-                        uf[i] -= l * uf[i - 1];
+                        const double ai = a[i] - x;
+                        const double e2 = e[i - 1] * e[i - 1];
+                        const double p2 = ai * p1 - e2 * p0;
+                        const double d2 = ai * d1 - p1 - e2 * d0;
+                        const double h2 = ai * h1 - 2.0 * d1 - e2 * h0;
+                        p0 = p1; p1 = p2;
+                        d0 = d1; d1 = d2;
+                        h0 = h1; h1 = h2;
+                        const double mag = fmax(fabs(p1), fmax(fabs(d1), fabs(h1)));
+                        if (mag > 0x1p+400 || (mag < 0x1p-400 && mag > 0.0)) {
+                            int ex;
+                            frexp(mag, &ex);
+                            p0 = ldexp(p0, -ex); p1 = ldexp(p1, -ex);
+                            d0 = ldexp(d0, -ex); d1 = ldexp(d1, -ex);
+                            h0 = ldexp(h0, -ex); h1 = ldexp(h1, -ex);
+                        }
                     }
-                    uf[k - 1] /= mf[k - 1];
-                    for (int i = k - 2; i >= 0; --i) uf[i] = (uf[i] - (float)e[i] * uf[i + 1]) / mf[i];
-                    float mx = 0.0f;
-                    for (int i = 0; i < k; ++i) mx = fmaxf(mx, fabsf(uf[i]));
-                    const float inv = 1.0f / mx;
-                    for (int i = 0; i < k; ++i) uf[i] *= inv;
+                    if (p1 == 0.0) break;                         // x is an eigenvalue
+                    const double G = d1 / p1;
+                    const double H = G * G - h1 / p1;
+                    const double disc = sqrt(fmax(0.0, (kk - 1.0) * (kk * H - G * G)));
+                    const double den = (G < 0.0) ? G - disc : G + disc;
+                    if (den == 0.0 || !isfinite(den)) break;
+                    const double step = kk / den;
+                    const double xn = x - step;
+                    if (!(xn >= x) || !(xn < s_hi + margin)) break;   // must climb, stay in the bracket
+                    x = xn;
+                    if (fabs(step) <= 8.0 * DBL_EPSILON) break;
                 }
-                // widen to FP64 in place (back to front: u and uf share storage)
-                for (int i = k - 1; i >= 0; --i) u[i] = (double)uf[i];
-                double num = 0.0, den = 0.0;
-                for (int i = 0; i < k; ++i) {
-                    double tu = a[i] * u[i];
-                    if (i > 0) tu += e[i - 1] * u[i - 1];
-                    if (i < k - 1) tu += e[i] * u[i + 1];
-                    num += u[i] * tu;
-                    den += u[i] * u[i];
-                }
-                xi = (num / den) * scale;
-                const double nrm = 1.0 / sqrt(den);
-                for (int i = 0; i < k; ++i) u[i] *= nrm;
+                xi = x * scale;
+                sigma = x - 16.0 * DBL_EPSILON;
             } else {
-            // FP64 Laguerre iteration on p_k(x) of the scaled matrix, from left of the
-            // bracket (cubic, and monotone to the smallest root even through clusters);
-            // eigenvalues of the scaled matrix are accurate to ~eps in absolute terms,
-            // so the stopping test is absolute
-            const double margin = 256.0 * FLT_EPSILON;
-            const double kk = (double)k;
-            double x = s_lo - margin;
-            for (int it = 0; it < 40; ++it) {
-                double p0 = 1.0, p1 = a[0] - x;               // p_0, p_1
-                double d0 = 0.0, d1 = -1.0;                   // first derivatives
-                double h0 = 0.0, h1 = 0.0;                    // second derivatives
-                for (int i = 1; i < k; ++i) {
-                    const double ai = a[i] - x;
-                    const double e2 = e[i - 1] * e[i - 1];
-                    const double p2 = ai * p1 - e2 * p0;
-                    const double d2 = ai * d1 - p1 - e2 * d0;
-                    const double h2 = ai * h1 - 2.0 * d1 - e2 * h0;
-                    p0 = p1; p1 = p2;
-                    d0 = d1; d1 = d2;
-                    h0 = h1; h1 = h2;
-                    const double mag = fmax(fabs(p1), fmax(fabs(d1), fabs(h1)));
-                    if (mag > 0x1p+400 || (mag < 0x1p-400 && mag > 0.0)) {
-                        int ex;
-                        frexp(mag, &ex);
-                        p0 = ldexp(p0, -ex); p1 = ldexp(p1, -ex);
-                        d0 = ldexp(d0, -ex); d1 = ldexp(d1, -ex);
-                        h0 = ldexp(h0, -ex); h1 = ldexp(h1, -ex);
-                    }
-                }
-                if (p1 == 0.0) break;                         // x is an eigenvalue
-                const double G = d1 / p1;
-                const double H = G * G - h1 / p1;
-                const double disc = sqrt(fmax(0.0, (kk - 1.0) * (kk * H - G * G)));
-                const double den = (G < 0.0) ? G - disc : G + disc;
-                if (den == 0.0 || !isfinite(den)) break;
-                const double step = kk / den;
-                const double xn = x - step;
-                if (!(xn >= x) || !(xn < s_hi + margin)) break;   // must climb, stay in the bracket
-                x = xn;
-                if (fabs(step) <= 8.0 * DBL_EPSILON) break;
+                // FP32 path: the shift just below the FP32 bracket; the eigenvector
+                // and the Rayleigh quotient below are FP64
+                sigma = s_lo - 2.0 * (s_hi - s_lo) - 64.0 * FLT_EPSILON;
             }
-            xi = x * scale;
-            // inverse iteration on T - sigma I, sigma just below the root
-            const double sigma = x - 16.0 * DBL_EPSILON;
+            // inverse iteration on T - sigma I = L U, sigma below the smallest
+            // eigenvalue: U has the pivots m_i on its diagonal and e_i above it, L the
+            // multipliers l_i = e_{i-1} / m_{i-1} below its unit diagonal; m[] keeps 1 / m_i
             const double tiny = DBL_EPSILON * 1e-3;
-            for (int i = 0; i < k; ++i) u[i] = 1.0;
-            for (int it = 0; it < 3; ++it) {
+            {
                 double mm = a[0] - sigma;
                 if (fabs(mm) < tiny) mm = tiny;
-                m[0] = mm;
+                m[0] = 1.0 / mm;
                 for (int i = 1; i < k; ++i) {
                     const double es = e[i - 1];
-                    const double l = es / m[i - 1];
-                    mm = (a[i] - sigma) - l * es;
+                    mm = (a[i] - sigma) - es * es * m[i - 1];
                     if (fabs(mm) < tiny) mm = tiny;
-                    m[i] = mm;
-                    u[i] -= l * u[i - 1];
+                    m[i] = 1.0 / mm;
                 }
-                u[k - 1] /= m[k - 1];
-                for (int i = k - 2; i >= 0; --i) u[i] = (u[i] - e[i] * u[i + 1]) / m[i];
+            }
+            // three solves, then one normalisation: each solve grows u by at most
+            // 1 / min pivot (< 2^64 with the clamp below 1e-19), so u stays finite
+            for (int i = 0; i < k; ++i) u[i] = 1.0;
+            for (int it = 0; it < 3; ++it) {
+                for (int i = 1; i < k; ++i) u[i] -= e[i - 1] * m[i - 1] * u[i - 1];
+                u[k - 1] *= m[k - 1];
+                for (int i = k - 2; i >= 0; --i) u[i] = (u[i] - e[i] * u[i + 1]) * m[i];
+            }
+            {
                 double mx = 0.0;
                 for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(u[i]));
+                const double imx = 1.0 / mx;
                 double nrm = 0.0;
                 for (int i = 0; i < k; ++i) {
-                    u[i] /= mx;
+                    u[i] *= imx;
                     nrm += u[i] * u[i];
                 }
                 nrm = 1.0 / sqrt(nrm);
                 for (int i = 0; i < k; ++i) u[i] *= nrm;
             }
+            if constexpr (!LAGUERRE) {
+                // the Ritz value: FP64 Rayleigh quotient of the unit FP64 vector (its
+                // error is quadratic in the vector's)
+                double num = 0.0;
+                for (int i = 0; i < k; ++i) {
+                    double tu = a[i] * u[i];
+                    if (i > 0) tu += e[i - 1] * u[i - 1];
+                    if (i < k - 1) tu += e[i] * u[i + 1];
+                    num += u[i] * tu;
+                }
+                xi = num * scale;
             }
         }
     }
