@@ -4,19 +4,25 @@
 Workload (the single-GPU MaxCut configuration): random sparse graph
 G(n = 2^20, m = 3n) with weights +1/-1 (50/50), CSR int32, sketch rank R = 10,
 T = 2000 iterations of Alg. 6.1, FP32 vectors / matvecs / sketch with FP64
-reductions and dual state; compared against the FP64 path of the same library.
+reductions, tridiagonal eigenpair and dual state; compared against the FP64
+path of the same library.
 
 One step = one full solve through the C ABI: create the handle from the CSR
 (already resident in HBM), T iterations, Nystrom reconstruction and rounding.
 `value` is iterations per second over all ranks (replicas on N GPUs, weak
 scaling).  `e2e` repeats the solve from host buffers with the host<->device
-copies inside the timed region.  The reference arm (`--impl reference`) times
-the FP64 CPU oracle on a bounded sample of the same workload.  `serving` runs
-the first 256 requests of the batched-serving workload (Poisson arrivals at
-200 req/s, MaxCut graphs with n log-uniform in [100, 50000]) through the
-server API: solves/s and p50/p99 latency.  `phase_retrieval` solves the
-coded-diffraction phase-retrieval workload (n = 2^16, 12 masks) in FP32 and FP64
-and puts its D-matvec against the FP32 ALU roofline.  `large_maxcut` solves the
+copies inside the timed region.  `roofline` is the Lanczos step (the tiled
+D-matvec passes and the three-term update) against the measured HBM copy
+rate.  `equal_gap_1e-3` runs both precisions to relative gap and
+infeasibility <= 1e-3 (Eq. E.1) on the n = 800 graph, where both get there;
+`equal_gap_1e-1_er2p20` does the same to 1e-1 on the headline graph.  The
+reference arm (`--impl reference`) times the FP64 CPU oracle on a bounded
+sample of the same workload.  `serving` runs the first 256 requests of the
+batched-serving workload (Poisson arrivals at 200 req/s, MaxCut graphs with n
+log-uniform in [100, 50000]) through the server API: solves/s and p50/p99
+latency, with an FP32-vs-FP64 twin on the first 64.  `phase_retrieval` solves
+the coded-diffraction workload (n = 2^16, 12 masks) in FP32 and FP64 and puts
+its D-matvec against the FP32 ALU roofline.  `large_maxcut` solves the
 n = 2^23 torus MaxCut (T = 1000) from HBM-resident CSR.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
@@ -51,41 +57,44 @@ def lanczos_q(t: int, n: int) -> int:
     return int(min(math.ceil(t ** 0.25 * math.log(n)), n - 1))
 
 
-def launches_per_solve(n: int, T: int) -> int:
-    """Kernels of one solve: per iteration 2q+3 (q D-matvec steps, q-1 updates,
-    tridiagonal, Ritz, fused z/sketch update, dual+start); create 6; reconstruct 13."""
-    return sum(2 * lanczos_q(t, n) + 3 for t in range(1, T + 1)) + 6 + 13
+def launches_per_solve(n: int, T: int, tiled: bool) -> int:
+    """Kernels of one solve: per iteration q D-matvec steps (two launches each on
+    the tiled layout), q-1 updates, tridiagonal, Ritz, fused z/sketch update,
+    dual+start; create 6; reconstruct 13."""
+    per_step = 2 if tiled else 1
+    return sum((per_step + 1) * lanczos_q(t, n) + 3 for t in range(1, T + 1)) + 6 + 13
 
 
-def spmv_bytes(n: int, nnz: int) -> int:
-    """Algorithmic bytes of one D-matvec step (FP32, signs packed in the column
-    index): row_ptr 4(n+1) + col 4 nnz + x 4n (each entry at least once) +
-    dvec 4n + output 4n."""
-    return 4 * (n + 1) + 4 * nnz + 12 * n
+def lanczos_step_bytes(n: int, nnz: int) -> int:
+    """Algorithmic bytes of one FP32 Lanczos step (D-matvec + three-term update)
+    at the per-unit figure of the hot-path scope: 4(n+1) row_ptr + 4 nnz col +
+    4 nnz val + 4n x (one pass) + 4n dvec + 4n out + 16n update = 8 nnz + 32n."""
+    return 8 * nnz + 32 * n
 
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ("k_maxcut.cu", "common.cuh", "internal.h"):
+    for f in ("k_tiled.cu", "k_lanczos.cu", "k_maxcut.cu", "common.cuh", "internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1912_02949_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic():
-    """DRAM bytes per launch of the D-matvec step from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "spmv_step_er2p20.txt")
+    """DRAM bytes of one Lanczos step (the two tiled passes and the update) from
+    the committed ncu summary, if it was taken on the current kernel source;
+    else None."""
+    path = os.path.join(ROOT, "profiles", "lanczos_step_er2p20.md")
     if not os.path.exists(path):
         return None
     vals = {}
     for line in open(path):
         if ":" in line:
             k, v = line.split(":", 1)
-            vals[k.strip()] = v.strip()
+            vals[k.strip().strip("*- ")] = v.strip().strip("`")
     if vals.get("kernel_source_sha") != kernel_source_sha():
         return None
     try:
-        return int(float(vals["dram_bytes_per_launch"]))
+        return int(float(vals["dram_bytes_per_step"]))
     except (KeyError, ValueError):
         return None
 
@@ -114,7 +123,7 @@ SERVE_DESC = ("batched serving slice: Poisson arrivals at 200 req/s, n log-unifo
               "degree U[4, 16], unit weights, R=10, solved to relative gap 1e-3 (T_max=3000), FP32 path")
 
 
-def run_serving(S, count: int, slots: int, seed: int, T_max: int = 3000):
+def run_serving(S, count: int, slots: int, seed: int, T_max: int = 3000, precision: int = 32):
     """The first `count` requests of the batched-serving workload through the
     server API (submit at the arrival times, poll every result).  Returns the
     throughput / latency summary and the raw latencies (ms)."""
@@ -132,7 +141,8 @@ def run_serving(S, count: int, slots: int, seed: int, T_max: int = 3000):
     for r, (rp, col) in zip(reqs, graphs):
         while time.perf_counter() - t0 < r["arrival_s"]:
             time.sleep(0.0002)
-        prm = S.scgal_params_default(R=10, T_max=T_max, tol=1e-3, precision=32, seed=r["seed"], instance=r["id"])
+        prm = S.scgal_params_default(R=10, T_max=T_max, tol=1e-3, precision=precision, seed=r["seed"],
+                                     instance=r["id"])
         tickets.append(S.scgal_submit(srv, rp, col, None, r["n"], col.size, prm))
     res = [S.scgal_poll(srv, t, -1) for t in tickets]
     wall = time.perf_counter() - t0
@@ -148,8 +158,38 @@ def run_serving(S, count: int, slots: int, seed: int, T_max: int = 3000):
            "queue_p50_ms": float(np.percentile([x["queue_ms"] for x in res], 50)),
            "rounds": st["rounds"], "worker_ms": {"wait": st["wait_ms"], "admit": st["admit_ms"],
                                                   "retire": st["retire_ms"]},
-           "device_bytes_peak": st["device_bytes_peak"], "desc": SERVE_DESC}
+           "device_bytes_peak": st["device_bytes_peak"], "precision": precision,
+           "desc": SERVE_DESC.replace("FP32 path", f"FP{precision} path")}
     return out, lat.tolist()
+
+
+def equal_gap_leg(S, g, tol: float, T_max: int, stream, desc: str, graph_bufs=None) -> dict:
+    """FP32 and FP64 solves of graph g until relative gap and infeasibility are
+    both <= tol (Eq. E.1) or T_max: iterations, seconds (CUDA events on the
+    handle's stream, create to the stopping iteration) and the time ratio."""
+    import torch
+    rp, col, val = g.csr()
+    if graph_bufs is None:
+        graph_bufs = (rp, col, None if g.weight_kind == "unit" else val)
+    out = {"desc": desc, "tol": tol, "T_max": T_max}
+    for prec in (32, 64):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = S.scgal_create_maxcut(graph_bufs[0], graph_bufs[1], graph_bufs[2], g.n, int(col.size), 0.0,
+                                  S.scgal_params_default(R=R, T_max=T_max, precision=prec, seed=SEED, tol=tol))
+        S.scgal_set_stream(h, stream.cuda_stream)
+        rc, last = S.scgal_solve(h, T_max)
+        e1.record(stream)
+        e1.synchronize()
+        h.close()
+        it = last["t"] - 1 if last["converged"] else last["t"]
+        out[f"fp{prec}"] = {"converged": bool(last["converged"]), "iterations": it,
+                            "seconds": e0.elapsed_time(e1) / 1000.0, "relgap": last["relgap"],
+                            "infeas": last["infeas"]}
+    if out["fp32"]["converged"] and out["fp64"]["converged"]:
+        out["fp32_over_fp64_time_to_gap"] = out["fp64"]["seconds"] / out["fp32"]["seconds"]
+    return out
 
 
 def aggregate_serving(local, lat, world: int):
@@ -403,12 +443,54 @@ def oracle_rate(sample: dict, T: int) -> float:
     return 1.0 / (per_iter * q_full / q_sample)
 
 
-def cpu_baseline_entry(sample: dict, T: int) -> dict:
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_cpu_all_cores(iters: int, procs: int) -> dict:
+    """`procs` independent oracle samples at once, one single-threaded process
+    per core (the oracle itself is unchanged): aggregate iterations per second of
+    independent solves on all host cores."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", str(iters), "--cpu-reps", "1"]
+    t0 = time.perf_counter()
+    ps = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, env=env)
+          for _ in range(procs)]
+    outs = [json.loads(p.communicate()[0].strip().splitlines()[-1]) for p in ps]
+    wall = time.perf_counter() - t0
+    return {"procs": procs, "samples": outs, "wall_s": wall}
+
+
+def cpu_baseline_entry(sample: dict, T: int, all_cores: dict | None = None) -> dict:
     secs = sum(sample["samples"]) + sample["fixed_plus_one"]
-    return {"value": oracle_rate(sample, T), "unit": "iter/s", "cores": 1, "kind": "oracle",
-            "sample": (f"iterations 2..{sample['iters']} of the same n=2^20 solve on one host core "
-                       f"({len(sample['samples'])} run(s) of T={sample['iters']} minus a T=1 run, {secs:.1f} s "
-                       f"in total); rate scaled to the full T={T} run by Lanczos steps per iteration")}
+    out = {"value": oracle_rate(sample, T), "unit": "iter/s", "cores": 1, "kind": "oracle",
+           "extrapolated": True, "cpu_model": cpu_model(), "host_cores": os.cpu_count(),
+           "sample": (f"iterations 2..{sample['iters']} of the same n=2^20 solve on one host core "
+                      f"({len(sample['samples'])} run(s) of T={sample['iters']} minus a T=1 run, {secs:.1f} s "
+                      f"in total); rate extrapolated to the full T={T} run by Lanczos steps per iteration")}
+    if all_cores:
+        rates = [oracle_rate(x, T) for x in all_cores["samples"]]
+        out["all_cores"] = {"value": sum(rates), "unit": "iter/s", "cores": all_cores["procs"],
+                            "extrapolated": True,
+                            "sample": (f"{all_cores['procs']} independent single-threaded oracle processes at "
+                                       f"once, each the sample above ({all_cores['wall_s']:.1f} s wall); the sum "
+                                       f"of their extrapolated rates (independent solves, not one faster solve)")}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -447,7 +529,7 @@ def profile_solve(T: int):
     rc, last = S.scgal_solve(h, T)
     S.scgal_reconstruct(h)
     print(json.dumps({"T": T, "seconds": time.perf_counter() - t0, "relgap": last["relgap"],
-                      "launches": launches_per_solve(g.n, T)}))
+                      "launches": launches_per_solve(g.n, T, S.scgal_get_info(h)["spmv_kind"] == S.SCGAL_SPMV_TILED)}))
     h.close()
 
 
@@ -492,9 +574,13 @@ def main():
     ap.add_argument("--sample-iters", type=int, default=6)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-procs", type=int, default=16,
+                    help="independent oracle processes of the all-core CPU figure (capped at the host's cores)")
     ap.add_argument("--serve-requests", type=int, default=256,
                     help="requests of the batched-serving slice (0: skip the serving leg)")
     ap.add_argument("--serve-slots", type=int, default=152)
+    ap.add_argument("--serve-twin", type=int, default=64,
+                    help="requests of the FP32-vs-FP64 serving comparison (0: skip)")
     ap.add_argument("--no-phase", action="store_true", help="skip the phase-retrieval leg")
     ap.add_argument("--no-large", action="store_true", help="skip the n = 2^23 torus MaxCut leg")
     ap.add_argument("--no-ptycho", action="store_true", help="skip the Fourier-ptychography leg")
@@ -612,14 +698,19 @@ def main():
         ms64, last64, cut64, _, _ = solve(64)
         extra["fp64"] = {"iter_per_s": T / (ms64 / 1000.0), "relgap_T": last64["relgap"],
                          "infeas_T": last64["infeas"], "best_cut": cut64, "ms_per_solve": ms64}
-        gap = {}
-        for prec in (32, 64):
-            ms_g, last_g, _, _, _ = solve(prec, tol=1e-3)
-            it = last_g["t"] - 1 if last_g["converged"] else last_g["t"]
-            gap[f"fp{prec}"] = {"converged": bool(last_g["converged"]), "iterations": it,
-                                "seconds": ms_g / 1000.0, "relgap": last_g["relgap"], "infeas": last_g["infeas"]}
-        extra["equal_gap_1e-3"] = gap
-        extra["fp32_over_fp64"] = value / world / extra["fp64"]["iter_per_s"]
+        extra["equal_gap_1e-3"] = equal_gap_leg(S, W.config_graph("er800", seed=SEED), 1e-3, 10000, stream,
+                                                "er800 (G(800, 19176), unit weights): both paths to relative gap "
+                                                "and infeasibility <= 1e-3")
+        if args.workload == "er2p20":
+            extra["equal_gap_1e-1_er2p20"] = equal_gap_leg(
+                S, g, 1e-1, 4000, stream,
+                "the headline n=2^20 graph: both paths to relative gap and infeasibility <= 1e-1 (1e-3 takes "
+                "beyond 12,000 iterations on this graph: gap 5e-3, infeasibility 1.5e-2 at t = 12,000)",
+                graph_bufs=(d_rp, d_col, d_w))
+        eg = extra["equal_gap_1e-3"]
+        extra["fp32_over_fp64"] = (eg["fp64"]["seconds"] / eg["fp32"]["seconds"]
+                                   if eg["fp32"]["converged"] and eg["fp64"]["converged"] else None)
+        extra["fp32_over_fp64_same_T"] = value / world / extra["fp64"]["iter_per_s"]
 
     # end to end from host buffers (pinned), copies inside the timed region
     ms_e2e, last_e, _, _, _ = solve(32, host=True)
@@ -659,16 +750,23 @@ def main():
     info = S.scgal_get_info(h)
     h.close()
     peak, peak_src = measured_peaks()
-    bytes_step = spmv_bytes(n, nnz)
-    achieved = bytes_step / (kern["spmv_step"] * 1e-3) / 1e9
+    # the Lanczos step (D-matvec passes + three-term update): the unit of the
+    # hot path's bytes (8 nnz + 32 n), timed as its kernels' CUDA-event sum
+    bytes_step = lanczos_step_bytes(n, nnz)
+    step_ms = kern["spmv_step"] + kern["lanczos_update"]
+    achieved = bytes_step / (step_ms * 1e-3) / 1e9
     qs = [lanczos_q(t, n) for t in range(1, T + 1)]
     per_solve_ms = sum(times) / args.steps
     share = {"spmv_step": kern["spmv_step"] * sum(qs) / per_solve_ms,
              "lanczos_update": kern["lanczos_update"] * (sum(qs) - T) / per_solve_ms,
              "ritz": kern["ritz"] * T / per_solve_ms, "tridiag": kern["tridiag"] * T / per_solve_ms}
+    tiled = info["spmv_kind"] == S.SCGAL_SPMV_TILED
+    kname = ("k_tile_products + k_tile_rows (tiled D-matvec, omega) + k_lanczos_update" if tiled else
+             "k_spmv_step (CSR D-matvec, omega) + k_lanczos_update")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(), "kernel": "k_spmv_step (CSR D-matvec + omega reduction)",
-                "bytes_per_launch": bytes_step, "ms_per_launch": kern["spmv_step"], "peak_source": peak_src}
+                "traffic": profiled_traffic() if tiled else None, "kernel": "Lanczos step: " + kname,
+                "bytes_per_launch": bytes_step, "ms_per_launch": step_ms, "peak_source": peak_src,
+                "dmatvec_ms": kern["spmv_step"], "update_ms": kern["lanczos_update"]}
 
     large = None
     if not args.no_large and args.workload == "er2p20":
@@ -686,10 +784,21 @@ def main():
     if args.serve_requests > 0:
         local, lat = run_serving(S, args.serve_requests, args.serve_slots, seed=replica_seed(rank))
         serving = aggregate_serving(local, lat, world)
+        serving["cap"] = (f"the first {args.serve_requests} of the workload's 4,096 requests, so that the default "
+                          f"run ends within minutes (--serve-requests 4096 runs all of them)")
+        if args.serve_twin > 0:
+            # the plain FP64 path on the same requests (the batched engine is FP32: FP64
+            # requests run on their own iteration graphs), against the FP32 path on that slice
+            tw32, _ = run_serving(S, args.serve_twin, args.serve_slots, seed=replica_seed(rank))
+            tw64, _ = run_serving(S, args.serve_twin, args.serve_slots, seed=replica_seed(rank), precision=64)
+            serving["twin"] = {"requests": args.serve_twin, "fp32": tw32, "fp64": tw64,
+                               "fp32_over_fp64_solves_per_s": tw32["solves_per_s"] / tw64["solves_per_s"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "er2p20":
-        cpu = cpu_baseline_entry(run_cpu_sample(args.sample_iters), T)
+        procs = max(1, min(os.cpu_count() or 1, args.cpu_procs))
+        cpu = cpu_baseline_entry(run_cpu_sample(args.sample_iters), T,
+                                 run_cpu_all_cores(args.sample_iters, procs) if procs > 1 else None)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
@@ -700,9 +809,10 @@ def main():
                            "n": n, "m": g.m, "nnz": nnz, "R": R,
                            "T": T, "precision": "fp32 vectors/matvec/sketch, fp64 reductions and dual state",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                           "l2": L2_NOTE, "spmv_lanes_per_row": info["spmv_group"]},
+                           "l2": L2_NOTE, "spmv": "tiled" if tiled else "gather",
+                           "tiled_slots": info["tiled_slots"]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps * launches_per_solve(n, T),
+                "gpu_launches": args.steps * launches_per_solve(n, T, tiled),
                 "clocks": clk, "solve": {"relgap_T": last["relgap"], "infeas_T": last["infeas"],
                                          "objective_T": last["p"], "best_cut": cut, "lambda_top3": list(lam[:3])},
                 "kernels_ms_per_launch": kern, "kernel_share_of_solve": share, "serving": serving, "phase_retrieval": phase, "ptychography": ptycho, "large_maxcut": large, **extra}
