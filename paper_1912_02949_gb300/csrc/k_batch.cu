@@ -640,8 +640,8 @@ static_assert(BATCH_NMIN_CL <= BATCH_NMAX_Y + 1, "one-block instances keep D x i
 __shared__ double b_cred[2][RED_NV];            // this block's totals for the cluster sums (two alternating sets)
 
 // Cluster barrier with every earlier write of this thread made visible first.
-// (The barrier alone did not order the blocks' writes here: without the fence,
-// four-block clusters gave run-to-run different results on GB300.)
+// (The barrier's own release / acquire semantics order these writes already; the
+// fence stays as a margin for the global data other SMs read back through L2.)
 __device__ __forceinline__ void csync() {
     __threadfence();
     cg::this_cluster().sync();
@@ -1069,6 +1069,9 @@ __device__ __forceinline__ void run_instance_cl(const BatchSlot& B, int iters, u
         const int q = p.qtab[t - 1];
         const int lz = c_lanczos<NARROW, WK>(B, q, cx);
         if (lz == 2) break;
+        // the last step's omega and k were written by thread 0 of block 0 after the
+        // step's last barrier; every thread of block 0 reads them in the solve
+        __syncthreads();
         if (cx.rank == 0) tridiag_body<float>(p, q, tsm);
         csync();                                 // coefficients, xi, stopping decision
         if (__ldcg(&sc->converged)) break;

@@ -1,0 +1,70 @@
+"""Stress check of the batched engine's four-block clusters (instances with
+n >= 16,384): identical requests give bitwise identical results, solved alone
+one after another and solved several at once beside other instances.
+
+Each request runs Alg. 6.1 for a fixed T (no early stop), so every result field
+but the timings must agree exactly.  The clusters' Lanczos runs end with block
+0's thread 0 writing the step's omega and Lanczos length, which every thread of
+that block then reads in the tridiagonal solve; a missing block barrier there
+once made these results differ from run to run.
+"""
+import time
+
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+T = 300
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_1912_02949_gb300 import build, scgal
+    build.build()
+    scgal.load()
+    return scgal
+
+
+def _fields(r):
+    return {k: v for k, v in r.items() if k not in ("queue_ms", "latency_ms")}
+
+
+def _case(n, m, seed):
+    g = W.er_graph(n, m, seed=seed, weights="unit")
+    rp, col, _ = g.csr()
+    return g, rp, col
+
+
+def _submit(S, srv, case, seed):
+    g, rp, col = case
+    prm = S.scgal_params_default(R=10, T_max=T, tol=0.0, precision=32, seed=seed, instance=seed)
+    return S.scgal_submit(srv, rp, col, None, g.n, col.size, prm)
+
+
+def test_clustered_instances_identical_alone_and_mixed(S):
+    big = {20000: _case(20000, 80000, 71), 40000: _case(40000, 160000, 72)}
+    small = [_case(3000, 12000, 73 + k) for k in range(4)]
+    srv = S.scgal_server_create(1 << 34, 32)
+    alone = {}
+    for n, case in big.items():                   # alone, three times in a row
+        runs = [S.scgal_poll(srv, _submit(S, srv, case, n), -1) for _ in range(3)]
+        assert runs[0]["status"] == S.SCGAL_ENOTDONE and runs[0]["iterations"] == T
+        for r in runs[1:]:
+            assert _fields(r) == _fields(runs[0]), n
+        alone[n] = _fields(runs[0])
+    for rep in range(2):                          # three copies of each at once, beside small instances
+        tickets = []
+        for k in range(3):
+            for n, case in big.items():
+                tickets.append((n, _submit(S, srv, case, n)))
+            tickets.append((None, _submit(S, srv, small[k], 100 + k)))
+            time.sleep(0.001)
+        for n, t in tickets:
+            res = S.scgal_poll(srv, t, -1)
+            if n is not None:
+                assert _fields(res) == alone[n], (rep, n)
+    st = S.scgal_server_get_stats(srv)
+    assert st["rejected"] == 0
+    S.scgal_server_destroy(srv)
