@@ -70,6 +70,19 @@ enum { SCGAL_SPMV_AUTO = 0,    /* MaxCut D-matvec kernel chosen by the library: 
                                    in shared memory; SCGAL_EINVAL if the graph does not fit the
                                    tile encoding (n > 2^21 FP32 / 2^20 FP64, or n < 4) */
 
+enum { SCGAL_FFT_AUTO = 0,     /* coded-diffraction D-matvec kernel chosen by the library:
+                                   FP32: CLUSTER where the transform fits it; FP64: CLUSTER
+                                   when it takes 16-block clusters (n = 2^16); else PASSES */
+       SCGAL_FFT_PASSES = 1,   /* three kernels per D-matvec (column FFTs, row FFTs with the
+                                   weight, column inverse FFTs with the mask sum), through an
+                                   L x n scratch array; any n = 2^m >= 16 */
+       SCGAL_FFT_CLUSTER = 2 }; /* one kernel: a cluster of C blocks per mask runs the
+                                   four-step forward and inverse transforms in shared memory,
+                                   the transposes through distributed shared memory; C = the
+                                   smallest power of two leaving <= 8192 (FP32) / 4096 (FP64)
+                                   points per block, at most 16; needs n >= 256 and
+                                   n <= 2^17 (FP32) / 2^16 (FP64), else SCGAL_EINVAL */
+
 enum { SCGAL_K_EQ = 0,    /* A(X) = b: the model problem (Eq. 2.2, Alg. 6.1) */
        SCGAL_K_LEQ = 1 };  /* A(X) <= b componentwise: the general template of App. D with
                               K = {u : u <= b} (App. D.3 item 1), through the slack
@@ -111,6 +124,8 @@ typedef struct {
                                gather grid and keeps the faster */
     int32_t  spmv;          /* SCGAL_SPMV_*: MaxCut D-matvec kernel (default AUTO); ignored
                                by the phase-retrieval problems */
+    int32_t  fft;           /* SCGAL_FFT_*: coded-diffraction D-matvec kernel (default AUTO);
+                               ignored by the other problems */
 } scgal_params;
 
 /* One iteration record (Alg. 6.1 step t; stopping values of Eq. E.1 for the
@@ -142,6 +157,8 @@ typedef struct {
     int32_t spmv_grid;    /* blocks of the MaxCut D-matvec grid (fixed or tuned); 0 otherwise */
     int32_t spmv_kind;    /* MaxCut: SCGAL_SPMV_GATHER or SCGAL_SPMV_TILED in use; 0 otherwise */
     int64_t tiled_slots;  /* MaxCut tiled layout: stored entries plus padding slots; 0 otherwise */
+    int32_t fft_cluster;  /* coded diffraction: blocks per cluster of the one-kernel D-matvec
+                             (SCGAL_FFT_CLUSTER); 0 for the three-kernel path and otherwise */
 } scgal_info;
 
 /* Fill *p with the defaults listed above. */

@@ -224,6 +224,7 @@ int check_params(const scgal_params* p) {
     if (p->kset != SCGAL_K_EQ && p->kset != SCGAL_K_LEQ) return SCGAL_EINVAL;
     if (p->tune != 0 && p->tune != 1) return SCGAL_EINVAL;
     if (p->spmv != SCGAL_SPMV_AUTO && p->spmv != SCGAL_SPMV_GATHER && p->spmv != SCGAL_SPMV_TILED) return SCGAL_EINVAL;
+    if (p->fft != SCGAL_FFT_AUTO && p->fft != SCGAL_FFT_PASSES && p->fft != SCGAL_FFT_CLUSTER) return SCGAL_EINVAL;
     if (p->device >= 0) {
         int count = 0;
         if (cudaGetDeviceCount(&count) != cudaSuccess || p->device >= count) {
@@ -490,6 +491,22 @@ int phase_build(scgal_ctx* h, const double* masks, const double* b) {
     int planes = std::min(L, std::max(1, (2 * num_sms() + colblocks - 1) / colblocks));
     p.ph_mb = (L + planes - 1) / planes;
     p.ynplanes = (L + p.ph_mb - 1) / p.ph_mb;
+    // the one-kernel D-matvec (a cluster of blocks per mask) where the transform fits it
+    p.phC = 0;
+    if (h->prm.fft != SCGAL_FFT_PASSES) {
+        int C = phase_cluster_size<V>(m);
+        // AUTO: FP32 wherever the transform fits; FP64 (bound by its arithmetic
+        // rate) only with 16-block clusters, the one shape where it measured faster
+        if (h->prm.fft == SCGAL_FFT_AUTO && sizeof(R) == 8 && C < 16) C = 0;
+        if (C) {
+            p.phC = C;
+            if (prepare_phase_cluster<V>(p, L) <= 0) p.phC = 0;
+        }
+        if (!p.phC && h->prm.fft == SCGAL_FFT_CLUSTER)
+            return set_err(h, SCGAL_EINVAL, "the transform does not fit the clustered D-matvec kernel");
+    }
+    if (p.phC) p.ynplanes = L;   // one output plane per mask
+    h->phase_cluster = p.phC;
     Consts& c = h->c;
     c.kind = KIND_PHASE;
     c.n = n;
@@ -531,7 +548,26 @@ int phase_build(scgal_ctx* h, const double* masks, const double* b) {
     ALLOC(h, dtw, sizeof(V) * n);
     ALLOC(h, db, sizeof(double) * d);
     ALLOC(h, p.wvec, sizeof(R) * d);
-    ALLOC(h, p.fftbuf, sizeof(V) * d);
+    p.fftbuf = nullptr;
+    p.tw4 = nullptr;
+    if (p.phC) {
+        // four-step twiddles exp(-2 pi i k1 l2 / n) at l2 n1 + k1, from the exact
+        // residue k1 l2 mod n in FP64, rounded once
+        std::vector<V> h4((size_t)n);
+        for (int l2 = 0; l2 < p.n2; ++l2)
+            for (int k1 = 0; k1 < p.n1; ++k1) {
+                const long long e = ((long long)k1 * l2) & (n - 1);
+                const double ang = -2.0 * M_PI * (double)e / (double)n;
+                h4[(size_t)l2 * p.n1 + k1].x = (R)std::cos(ang);
+                h4[(size_t)l2 * p.n1 + k1].y = (R)std::sin(ang);
+            }
+        V* d4 = nullptr;
+        ALLOC(h, d4, sizeof(V) * n);
+        CUDA_TRY(h, cudaMemcpy(d4, h4.data(), sizeof(V) * n, cudaMemcpyHostToDevice));
+        p.tw4 = d4;
+    } else {
+        ALLOC(h, p.fftbuf, sizeof(V) * d);
+    }
     CUDA_TRY(h, cudaMemcpy(dm, hmask.data(), sizeof(V) * d, cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(dtw, htw.data(), sizeof(V) * n, cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(db, bint.data(), sizeof(double) * d, cudaMemcpyHostToDevice));
@@ -545,6 +581,7 @@ int phase_build(scgal_ctx* h, const double* masks, const double* b) {
     if (p3blocks > h->grid_elem) h->grid_spmv = p3blocks;
     const int p2blocks = (p.n2 / p.ph_rpb) * L;
     if (p2blocks > h->grid_spmv) h->grid_spmv = p2blocks;
+    if (p.phC * L > h->grid_spmv) h->grid_spmv = p.phC * L;   // blocks of the clustered kernel
     if (prepare_phase_kernels<V>(p)) return set_err(h, SCGAL_ECUDA, "phase-retrieval kernels: shared memory");
     return setup_state<V>(h);
 }
@@ -1574,6 +1611,7 @@ int scgal_get_info(scgal_t h, scgal_info* out) {
         out->spmv_kind = h->tiled_on ? SCGAL_SPMV_TILED : SCGAL_SPMV_GATHER;
         out->tiled_slots = h->tiled_on ? h->tiled_slots : 0;
     }
+    if (h->kind == KIND_PHASE) out->fft_cluster = h->phase_cluster;
     return SCGAL_OK;
 }
 

@@ -219,16 +219,16 @@ template <> struct CompSum<float> {
 };
 
 // --------------------------------------------------------------------------
-// Deterministic grid reduction of NV doubles (blockDim.x == SCGAL_BS; 1-D or
-// 2-D grids, blocks numbered blockIdx.y * gridDim.x + blockIdx.x).
+// Deterministic grid reduction of NV doubles (blockDim.x == BS, a multiple of
+// 32; 1-D or 2-D grids, blocks numbered blockIdx.y * gridDim.x + blockIdx.x).
 // Returns true in exactly one block (the last to arrive); there tot[0..NV)
 // (shared memory) holds the grid totals for every thread after the call.
-template <int NV, typename WT = double>
+template <int NV, typename WT = double, int BS = SCGAL_BS>
 __device__ __forceinline__ bool grid_reduce(WT (&v)[NV], double* __restrict__ partials,
                                             unsigned* __restrict__ ticket, double* tot) {
     // WT: type of the warp-level sums (float on the FP32 path: FP64 arithmetic is
     // scarce on GB300); warp, block and grid totals are then added in FP64.
-    __shared__ double red[SCGAL_BS / 32][NV];
+    __shared__ double red[BS / 32][NV];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned nblk = gridDim.x * gridDim.y;
@@ -244,7 +244,7 @@ __device__ __forceinline__ bool grid_reduce(WT (&v)[NV], double* __restrict__ pa
     if (threadIdx.x < NV) {
         double s = 0.0;
 #pragma unroll
-        for (int w = 0; w < SCGAL_BS / 32; ++w) s += red[w][threadIdx.x];
+        for (int w = 0; w < BS / 32; ++w) s += red[w][threadIdx.x];
         partials[(size_t)threadIdx.x * nblk + bid] = s;
         __threadfence();   // this block's partials are visible before its ticket
     }
@@ -259,7 +259,7 @@ __device__ __forceinline__ bool grid_reduce(WT (&v)[NV], double* __restrict__ pa
     // fixed-order sum of the partials
     for (int k = 0; k < NV; ++k) {
         double s = 0.0;
-        for (unsigned b = threadIdx.x; b < nblk; b += SCGAL_BS) s += __ldcg(&partials[(size_t)k * nblk + b]);
+        for (unsigned b = threadIdx.x; b < nblk; b += BS) s += __ldcg(&partials[(size_t)k * nblk + b]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) red[wid][0] = s;
@@ -267,7 +267,7 @@ __device__ __forceinline__ bool grid_reduce(WT (&v)[NV], double* __restrict__ pa
         if (threadIdx.x == 0) {
             double t = 0.0;
 #pragma unroll
-            for (int w = 0; w < SCGAL_BS / 32; ++w) t += red[w][0];
+            for (int w = 0; w < BS / 32; ++w) t += red[w][0];
             tot[k] = t;
         }
         __syncthreads();
@@ -294,13 +294,15 @@ __device__ __forceinline__ void block_sum_to(WT v, double* out) {
     }
 }
 
-// Block-wide fixed-order sum of x[0..m) (every thread receives the total).
+// Block-wide fixed-order sum of x[0..m) (every thread receives the total;
+// blockDim.x == BS).
+template <int BS = SCGAL_BS>
 __device__ __forceinline__ double block_sum_array(const double* x, int m) {
-    __shared__ double red[SCGAL_BS / 32];
+    __shared__ double red[BS / 32];
     __shared__ double res;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double s = 0.0;
-    for (int b = threadIdx.x; b < m; b += SCGAL_BS) s += __ldcg(x + b);
+    for (int b = threadIdx.x; b < m; b += BS) s += __ldcg(x + b);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) red[wid] = s;
@@ -308,7 +310,7 @@ __device__ __forceinline__ double block_sum_array(const double* x, int m) {
     if (threadIdx.x == 0) {
         double t = 0.0;
 #pragma unroll
-        for (int w = 0; w < SCGAL_BS / 32; ++w) t += red[w];
+        for (int w = 0; w < BS / 32; ++w) t += red[w];
         res = t;
     }
     __syncthreads();

@@ -84,6 +84,8 @@ struct KP {
     int ph_rpb;         // rows per block in the row pass
     int ph_mb;          // masks per block in the last pass (ynplanes = ceil(L / ph_mb))
     int ynplanes;       // planes of ybuf summed to form D x (1 for MaxCut)
+    int phC;            // blocks per cluster of the clustered four-step kernel (0: three passes)
+    const V* tw4;       // n1 x n2 four-step twiddles exp(-2 pi i k1 l2 / n) at l2 n1 + k1 (phC > 0)
     // Fourier ptychography (KIND_PTYCHO): N x N image, M x M windows at offsets
     // (kr s, kc s) mod N, K = N / s windows per dimension; masks holds the pupil
     int fpN, fpM, fpS, fpK, fpLogM;
@@ -158,10 +160,10 @@ __device__ __forceinline__ void finish_lanczos_scalars(const KP<V>& p, int i, do
     sc->k = i + 1;
 }
 
-// The same for a last block of SCGAL_BS threads (all of them call it).
-template <typename V>
+// The same for a last block of BS threads (all of them call it).
+template <typename V, int BS = SCGAL_BS>
 __device__ __forceinline__ void finish_lanczos_step(const KP<V>& p, int i, double dot) {
-    const double rr = (i > 0) ? block_sum_array(p.upart, p.nupd) : 0.0;
+    const double rr = (i > 0) ? block_sum_array<BS>(p.upart, p.nupd) : 0.0;
     if (threadIdx.x == 0) finish_lanczos_scalars(p, i, dot, rr);
 }
 
@@ -183,6 +185,7 @@ struct scgal_ctx {
     int spmv_group = 8;
     long long tiled_slots = 0;  // slots of the tiled layout (0: none built)
     int tiled_on = 0;           // the iteration graphs use the tiled D-matvec
+    int phase_cluster = 0;      // blocks per cluster of the coded-diffraction D-matvec (0: three passes)
     int grid_elem = 1, grid_spmv = 1, grid_ritz = 1;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream the iteration graphs are captured on
@@ -245,6 +248,35 @@ template <typename V>
 int nystrom_reconstruct(const V* S, const V* Om, int n, int R, double tau, int trace_correct, double alpha,
                         double2* part, int grid, double2* G, double2* L, double2* M, double* scal,
                         typename VT<V>::D* Y, typename VT<V>::D* U, double* lam, double* err, cudaStream_t s);
+
+// Clustered coded-diffraction D-matvec (k_phase.cu): shared-memory layout of
+// one block of a C-block cluster.  Tile A holds n2 x CW (column phases; row
+// stride CW + 16 bytes, rows 16-byte aligned), tile B RW x n1 (row phase; row
+// stride n1 + 1), then the
+// block's rows of the weight (same stride as B) and the n1 roots of unity of
+// the length-n1 transform.  A doubles as the |X|^2 rows (RW x (n1 + 1) FP64)
+// of the primal update.
+struct PhcGeom {
+    int C, CW, RW, LDA, LDB;
+    unsigned offB, offW, offT, bytes;
+};
+__host__ __device__ inline unsigned phc_round16(size_t b) { return (unsigned)((b + 15) & ~(size_t)15); }
+__host__ __device__ inline PhcGeom phc_geom(int n1, int n2, int C, int vsz) {
+    PhcGeom g;
+    g.C = C;
+    g.CW = n1 / C;
+    g.RW = n2 / C;
+    g.LDA = g.CW + 16 / vsz;
+    g.LDB = n1 + 1;
+    const size_t a = (size_t)n2 * g.LDA * vsz, q = (size_t)g.RW * g.LDB * 8;
+    g.offB = phc_round16(a > q ? a : q);
+    g.offW = g.offB + phc_round16((size_t)g.RW * g.LDB * vsz);
+    g.offT = g.offW + phc_round16((size_t)g.RW * g.LDB * (vsz / 2));
+    g.bytes = g.offT + phc_round16((size_t)n1 * vsz);
+    return g;
+}
+template <typename V> int phase_cluster_size(int log2n);
+template <typename V> int prepare_phase_cluster(const KP<V>& p, int L);
 
 // MaxCut tiled D-matvec (k_tiled.cu)
 struct TiledGeom {

@@ -15,10 +15,15 @@
 // produce them, internal index j n + l2 n1 + l1 for measurement (j, l2 + n2 l1),
 // so P2 reads and writes them contiguously.
 #include <algorithm>
+#include <type_traits>
+
+#include <cooperative_groups.h>
 
 #include "internal.h"
 
 namespace scgal {
+
+namespace cg = cooperative_groups;
 
 template <typename V> struct CX;
 template <> struct CX<float2> {
@@ -108,6 +113,33 @@ __device__ void smem_fft(V* x, int lg, int batch, int es, int bs, const V* tws, 
             default: fft_stages<V, 1>(x, lg, s0, batch, es, bs, tws, sign); break;
         }
     }
+}
+
+// End of the primal-update pass (thread 0 of its last block): p and tau of
+// Eq. 6.2 (C = I, so v* C v = sC ||v||^2 and the scaled v v* / ||v||^2 adds
+// sC), and the dual step size of Eq. 6.4 from tot = (||z - wbar||^2,
+// <y, z - wbar>, ||y||^2), zero when the step would leave the ball ||y|| <= K.
+template <typename V>
+__device__ __forceinline__ void phase_update_finish(const KP<V>& p, const double* tot) {
+    DevScalars* sc = p.sc;
+    const Consts& c = p.c;
+    const double eta = sc->eta;
+    const int take = sc->take_h;
+    sc->vCv = c.sC;
+    sc->p = (1.0 - eta) * sc->p + (take ? eta * c.alpha * c.sC : 0.0);
+    sc->tau = (1.0 - eta) * sc->tau + (take ? eta * c.alpha : 0.0);
+    const double nzb2 = tot[0];
+    const long long t = sc->t;
+    double gamma = (nzb2 == 0.0) ? c.beta0
+                                 : fmin(c.beta0, 4.0 * c.alpha * c.alpha * c.beta0 * c.normA_s * c.normA_s /
+                                                     (pow((double)(t + 1), 1.5) * nzb2));
+    if (c.K_finite) {
+        const double yy = tot[2] + 2.0 * gamma * tot[1] + gamma * gamma * nzb2;
+        if (sqrt(yy) > c.K) gamma = 0.0;
+    }
+    sc->gamma = gamma;
+    sc->nzb2_new = nzb2;
+    p.hist[(t - 1) % c.hist_cap].gamma = gamma;
 }
 
 // P1: columns [cb*TC, cb*TC+TC) of mask j = blockIdx.y.
@@ -221,27 +253,8 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ph_p2(KP<V> p, const typename VT<V
         }
         double red[3] = {a_nzb, a_yzb, a_yy};
         __shared__ double tot[3];
-        if (grid_reduce_2d<3>(red, p.partials, p.ticket, tot)) {
-            if (threadIdx.x == 0) {
-                const Consts& c = p.c;
-                sc->vCv = c.sC;
-                sc->p = (1.0 - eta) * sc->p + (take ? eta * c.alpha * c.sC : 0.0);
-                sc->tau = (1.0 - eta) * sc->tau + (take ? eta * c.alpha : 0.0);
-                const double nzb2 = tot[0];
-                const long long t = sc->t;
-                double gamma = (nzb2 == 0.0)
-                                   ? c.beta0
-                                   : fmin(c.beta0, 4.0 * c.alpha * c.alpha * c.beta0 * c.normA_s * c.normA_s /
-                                                       (pow((double)(t + 1), 1.5) * nzb2));
-                if (c.K_finite) {
-                    const double yy = tot[2] + 2.0 * gamma * tot[1] + gamma * gamma * nzb2;
-                    if (sqrt(yy) > c.K) gamma = 0.0;
-                }
-                sc->gamma = gamma;
-                sc->nzb2_new = nzb2;
-                p.hist[(t - 1) % c.hist_cap].gamma = gamma;
-            }
-        }
+        if (grid_reduce_2d<3>(red, p.partials, p.ticket, tot))
+            if (threadIdx.x == 0) phase_update_finish(p, tot);
     }
 }
 
@@ -343,6 +356,587 @@ __global__ void k_wvec_nat(KP<V> p, const double* w) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p.c.d; i += (long long)gridDim.x * blockDim.x)
         p.wvec[i] = (Rt)(p.c.sA * w[i]);
 }
+
+// ---------------------------------------------------------------------------
+// Clustered four-step D-matvec and primal update: one thread-block cluster of C
+// blocks per mask.  Block r of the cluster holds columns [r CW, (r + 1) CW) of
+// the n2 x n1 array (k = k1 + n1 k2 at row k2, column k1) in the column phases
+// and rows l2 in [r RW, (r + 1) RW) in the row phase, CW = n1 / C, RW = n2 / C.
+// The two transposes between the phases are stores into the other blocks'
+// shared memory (distributed shared memory), each followed by one cluster
+// barrier; nothing but x, the masks, w, the twiddles and the output goes
+// through L2.
+//   column phase: length-n2 DFTs over k2 (Y[k1, l2]), times exp(-2 pi i k1 l2 / n)
+//   row phase:    length-n1 DFT over k1 -> W(psi_j x) at l = l2 + n2 l1, times
+//                 w_j, inverse length-n1 DFT over l1 -> G[l2, m1]
+//   column phase: times exp(+2 pi i l2 m1 / n), inverse length-n2 DFTs over l2
+//                 -> W*(...) at m = m1 + n1 m2, times conj(psi_j)
+// Forward transforms run decimation in frequency (natural order in, bit-reversed
+// out) and the inverse row transform decimation in time (bit-reversed in,
+// natural out), so no pass permutes data: w_j and the outputs are addressed
+// through the bit reversal instead.  A transform of length 2^lg runs in
+// ceil(lg / 4) passes ("groups") of 2..4 radix-2 stages, as even as possible.
+// A work item of a group holds the R = 2^NB elements at positions
+// pos0 | t << hb (t < R) in registers; in decimation in frequency the group's
+// stages are an R-point DFT over t (constant twiddles exp(-2 pi i k / R)) whose
+// slot t' then holds frequency brev(t') and is multiplied by
+// exp(-2 pi i low brev(t') / M), M = 2^(hb + NB), low = pos0 mod 2^hb; in
+// decimation in time the same twiddle multiplies slot t before the R-point
+// transform.  Mask j writes plane j of the output; the Lanczos update adds the
+// planes.
+
+// exp(-2 pi i k / 16) from cos(pi / 8), sin(pi / 8) and sqrt(1 / 2).
+__host__ __device__ constexpr double phc_c16(int k) {
+    constexpr double C1 = 0.92387953251128675613, S1 = 0.38268343236508977173, H = 0.70710678118654752440;
+    k &= 15;
+    return k == 0 ? 1.0 : k == 1 ? C1 : k == 2 ? H : k == 3 ? S1 : k == 4 ? 0.0 : k == 5 ? -S1 : k == 6 ? -H
+         : k == 7 ? -C1 : k == 8 ? -1.0 : k == 9 ? -C1 : k == 10 ? -H : k == 11 ? -S1 : k == 12 ? 0.0
+         : k == 13 ? S1 : k == 14 ? H : C1;
+}
+__host__ __device__ constexpr double phc_s16(int k) { return -phc_c16(k + 12); }   // -sin(2 pi k / 16)
+
+// a * exp(-+2 pi i k16 / 16) (INV: the conjugate root); k16 is a constant once
+// the callers' loops are unrolled, so the trivial roots cost no multiply.
+template <typename V, bool INV>
+__device__ __forceinline__ V phc_root16(V a, int k16) {
+    typedef typename VT<V>::R Rt;
+    k16 &= 15;
+    if (k16 == 0) return a;
+    V r;
+    if (k16 == 4) {   // -i (forward) / +i (inverse)
+        if (INV) { r.x = -a.y; r.y = a.x; }
+        else { r.x = a.y; r.y = -a.x; }
+        return r;
+    }
+    if (k16 == 8) { r.x = -a.x; r.y = -a.y; return r; }
+    if (k16 == 12) {  // +i (forward) / -i (inverse)
+        if (INV) { r.x = a.y; r.y = -a.x; }
+        else { r.x = -a.y; r.y = a.x; }
+        return r;
+    }
+    V w;
+    w.x = (Rt)phc_c16(k16);
+    w.y = (Rt)(INV ? -phc_s16(k16) : phc_s16(k16));
+    return CX<V>::mul(a, w);
+}
+
+template <int NB>
+__host__ __device__ constexpr int phc_brevc(int t) {
+    int r = 0;
+    for (int b = 0; b < NB; ++b) r |= ((t >> b) & 1) << (NB - 1 - b);
+    return r;
+}
+
+// R-point decimation-in-frequency DFT over the slots (natural in, slot t' holds
+// frequency brev(t')).
+template <typename V, int NB, bool INV>
+__device__ __forceinline__ void phc_small_dif(V (&v)[1 << NB]) {
+    constexpr int R = 1 << NB;
+#pragma unroll
+    for (int st = 0; st < NB; ++st) {
+        const int half = R >> (st + 1);
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            if (t & half) continue;
+            const V a = v[t], b = v[t + half];
+            v[t].x = a.x + b.x;
+            v[t].y = a.y + b.y;
+            V d;
+            d.x = a.x - b.x;
+            d.y = a.y - b.y;
+            v[t + half] = phc_root16<V, INV>(d, ((t & (half - 1)) << st) * (16 / R));
+        }
+    }
+}
+
+// R-point decimation-in-time DFT over the slots (slot t holds input brev(t),
+// natural out).
+template <typename V, int NB, bool INV>
+__device__ __forceinline__ void phc_small_dit(V (&v)[1 << NB]) {
+    constexpr int R = 1 << NB;
+#pragma unroll
+    for (int st = 0; st < NB; ++st) {
+        const int half = 1 << st;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            if (t & half) continue;
+            const V u = v[t];
+            const V tt = phc_root16<V, INV>(v[t + half], (t & (half - 1)) * (R / (2 * half)) * (16 / R));
+            v[t].x = u.x + tt.x;
+            v[t].y = u.y + tt.y;
+            v[t + half].x = u.x - tt.x;
+            v[t + half].y = u.y - tt.y;
+        }
+    }
+}
+
+// Slot t times exp(-+2 pi i low brev(t) / 2^(hb + NB)), from the full-length
+// table twf[k] = exp(-2 pi i k / 2^lgt) (lgt >= hb + NB).
+template <typename V, int NB, bool INV>
+__device__ __forceinline__ void phc_twiddle(V (&v)[1 << NB], int hb, int low, const V* twf, int lgt) {
+    if (hb == 0) return;
+    const int sh = lgt - hb - NB;
+#pragma unroll
+    for (int t = 1; t < (1 << NB); ++t) {
+        V w = twf[(low * phc_brevc<NB>(t)) << sh];
+        if (INV) w.y = -w.y;
+        v[t] = CX<V>::mul(v[t], w);
+    }
+}
+
+template <typename V, int NB, bool INV>
+__device__ __forceinline__ void phc_dif(V (&v)[1 << NB], int hb, int low, const V* twf, int lgt) {
+    phc_small_dif<V, NB, INV>(v);
+    phc_twiddle<V, NB, INV>(v, hb, low, twf, lgt);
+}
+template <typename V, int NB, bool INV>
+__device__ __forceinline__ void phc_dit(V (&v)[1 << NB], int hb, int low, const V* twf, int lgt) {
+    phc_twiddle<V, NB, INV>(v, hb, low, twf, lgt);
+    phc_small_dit<V, NB, INV>(v);
+}
+
+// Groups of a length-2^lg transform: ceil(lg / 4) of them, sizes as even as
+// possible (larger first); group gi starts at stage gstart (1-based).
+__host__ __device__ constexpr int phc_ngroups(int lg) { return (lg + 3) >> 2; }
+__host__ __device__ constexpr int phc_gsize(int lg, int gi) {
+    return lg / phc_ngroups(lg) + (gi < lg - (lg / phc_ngroups(lg)) * phc_ngroups(lg) ? 1 : 0);
+}
+__host__ __device__ constexpr int phc_gstart(int lg, int gi) {
+    return gi == 0 ? 1 : phc_gstart(lg, gi - 1) + phc_gsize(lg, gi - 1);
+}
+// hb of DIF group gi (its elements differ in position bits hb .. hb + NB - 1)
+__host__ __device__ constexpr int phc_ghb(int lg, int gi) { return lg - phc_gstart(lg, gi) - phc_gsize(lg, gi) + 1; }
+
+template <int NB>
+__device__ __forceinline__ int phc_pos0(int g, int hb) {
+    return ((g >> hb) << (hb + NB)) | (g & ((1 << hb) - 1));
+}
+
+// Distributed shared memory: the address of the same shared-memory location in
+// block `rank` of the cluster, and an 8- or 16-byte store there.
+__device__ __forceinline__ uint32_t phc_mapa(uint32_t a, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void phc_st_remote(uint32_t a, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y));
+}
+__device__ __forceinline__ void phc_st_remote(uint32_t a, double2 v) {
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.x), "d"(v.y));
+}
+
+__device__ __forceinline__ void phc_st_remote16(uint32_t a, float2 u, float2 v) {
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(u.x), "f"(u.y), "f"(v.x), "f"(v.y));
+}
+
+// Asynchronous global -> shared copies of 4, 8 or 16 bytes (both addresses
+// aligned to the size); phc_cp_wait_all waits for the thread's own copies.
+template <int BYTES>
+__device__ __forceinline__ void phc_cp_async(void* sdst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc), "n"(BYTES));
+}
+__device__ __forceinline__ void phc_cp_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void phc_cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void phc_cp_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Per-block view of the cluster kernel: with LG1 > 0 the transform shape
+// (n1 = 2^LG1, n2 = 2^LG2, C = 2^LGC) is a compile-time constant, else it is
+// read from the handle.
+template <typename V, int LG1, int LG2, int LGC>
+struct PhcK {
+    typedef typename VT<V>::R Rt;
+    static constexpr bool kFixed = LG1 > 0;   // shape compiled in: global loads are issued ahead of the FFT work
+    int lg1r, lg2r, lgCr;
+    int n, j, r;
+    V* A;
+    V* B;
+    Rt* W;
+    V* twf;   // exp(-2 pi i k / n1), k < n1
+    uint32_t A32, B32;
+    __device__ __forceinline__ int lg1() const { return LG1 ? LG1 : lg1r; }
+    __device__ __forceinline__ int lg2() const { return LG1 ? LG2 : lg2r; }
+    __device__ __forceinline__ int lgC() const { return LG1 ? LGC : lgCr; }
+    __device__ __forceinline__ int n1() const { return 1 << lg1(); }
+    __device__ __forceinline__ int n2() const { return 1 << lg2(); }
+    __device__ __forceinline__ int lgCW() const { return lg1() - lgC(); }
+    __device__ __forceinline__ int lgRW() const { return lg2() - lgC(); }
+    __device__ __forceinline__ int CW() const { return 1 << lgCW(); }
+    __device__ __forceinline__ int RW() const { return 1 << lgRW(); }
+    __device__ __forceinline__ int LDA() const { return CW() + 16 / (int)sizeof(V); }
+    __device__ __forceinline__ int LDB() const { return n1() + 1; }
+    __device__ __forceinline__ int c0() const { return r << lgCW(); }
+    __device__ __forceinline__ int l0() const { return r << lgRW(); }
+};
+
+// Runs f with the group size nb (2, 3 or 4) as a compile-time constant.
+template <typename F>
+__device__ __forceinline__ void phc_nb(int nb, F&& f) {
+    if (nb == 4) f(std::integral_constant<int, 4>{});
+    else if (nb == 3) f(std::integral_constant<int, 3>{});
+    else f(std::integral_constant<int, 2>{});
+}
+
+// Column phase, forward (DIF over k2), group gi.  The first group reads
+// psi_j .* x from global memory; the last multiplies by the four-step twiddle
+// and stores Y[k1, l2] into row l2 mod RW of the B tile of block l2 / RW.
+template <typename V, int NT, int NB, typename K>
+__device__ __forceinline__ void phc_col_fwd(const K& k, const KP<V>& p, const V* __restrict__ x, int gi, bool first,
+                                            bool last) {
+    constexpr int P = 1 << NB;
+    const int hb = phc_ghb(k.lg2(), gi);
+    const int items = k.CW() << (k.lg2() - NB);
+    const V* __restrict__ mask = p.masks + (size_t)k.j * k.n;
+    for (int it = threadIdx.x; it < items; it += NT) {
+        const int c = it & (k.CW() - 1), g = it >> k.lgCW();
+        const int pos0 = phc_pos0<NB>(g, hb);
+        V v[P], tw[P];
+        if (K::kFixed && last) {   // hb == 0: slot t will hold l2 = brev(pos0 + t)
+#pragma unroll
+            for (int t = 0; t < P; ++t) tw[t] = p.tw4[(size_t)brev(pos0 + t, k.lg2()) * k.n1() + k.c0() + c];
+        }
+        if (first) {
+            V xm[P];
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                const int e = k.c0() + c + (pos0 | (t << hb)) * k.n1();
+                xm[t] = x[e];
+                v[t] = mask[e];
+            }
+            if (K::kFixed) {   // one item per thread: the roots of unity are waited for here
+                phc_cp_wait_group<1>();
+                __syncthreads();
+            }
+#pragma unroll
+            for (int t = 0; t < P; ++t) v[t] = CX<V>::mul(xm[t], v[t]);
+        } else {
+#pragma unroll
+            for (int t = 0; t < P; ++t) v[t] = k.A[(pos0 | (t << hb)) * k.LDA() + c];
+        }
+        phc_dif<V, NB, false>(v, hb, g & ((1 << hb) - 1), k.twf, k.lg1());
+        if (last) {
+            const int k1 = k.c0() + c;
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                const int l2 = brev(pos0 + t, k.lg2());
+                const V val = CX<V>::mul(v[t], K::kFixed ? tw[t] : p.tw4[(size_t)l2 * k.n1() + k1]);
+                const uint32_t off = (uint32_t)(((l2 & (k.RW() - 1)) * k.LDB() + k1) * (int)sizeof(V));
+                phc_st_remote(phc_mapa(k.B32 + off, l2 >> k.lgRW()), val);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < P; ++t) k.A[(pos0 | (t << hb)) * k.LDA() + c] = v[t];
+        }
+    }
+}
+
+// Row phase: lanes run across rows (the padded row stride n1 + 1 keeps those
+// accesses free of bank conflicts, and a warp's twiddles are one broadcast).
+// Forward (DIF over k1), group gi < last.
+template <typename V, int NT, int NB, typename K>
+__device__ __forceinline__ void phc_row_fwd(const K& k, int gi) {
+    constexpr int P = 1 << NB;
+    const int hb = phc_ghb(k.lg1(), gi);
+    const int items = k.RW() << (k.lg1() - NB);
+    for (int it = threadIdx.x; it < items; it += NT) {
+        const int row = it & (k.RW() - 1), g = it >> k.lgRW();
+        const int pos0 = phc_pos0<NB>(g, hb);
+        V* rb = k.B + row * k.LDB();
+        V v[P];
+#pragma unroll
+        for (int t = 0; t < P; ++t) v[t] = rb[pos0 | (t << hb)];
+        phc_dif<V, NB, false>(v, hb, g & ((1 << hb) - 1), k.twf, k.lg1());
+#pragma unroll
+        for (int t = 0; t < P; ++t) rb[pos0 | (t << hb)] = v[t];
+    }
+}
+
+// Sends this block's rows of G (tile B, natural m1) to the A tiles of the
+// cluster: row l2 = l0 + row, column m1 goes to block m1 / CW.  Lanes run along
+// the rows with 16-byte stores (A's rows are 16-byte aligned).
+template <typename V, int NT, typename K>
+__device__ __forceinline__ void phc_push_rows(const K& k) {
+    constexpr int EP = 16 / (int)sizeof(V);   // points per store
+    constexpr int LEP = EP == 2 ? 1 : 0;
+    const int lpr = k.lg1() - LEP;           // log2 of the stores per row
+    for (int idx = threadIdx.x; idx < (k.RW() << lpr); idx += NT) {
+        const int row = idx >> lpr, m1 = (idx & ((1 << lpr) - 1)) << LEP;
+        const V* src = k.B + row * k.LDB() + m1;
+        const uint32_t off = (uint32_t)(((k.l0() + row) * k.LDA() + (m1 & (k.CW() - 1))) * (int)sizeof(V));
+        const uint32_t ra = phc_mapa(k.A32 + off, m1 >> k.lgCW());
+        if constexpr (EP == 2) phc_st_remote16(ra, src[0], src[1]);
+        else phc_st_remote(ra, src[0]);
+    }
+}
+
+// Row phase, the last forward group (hb = 0: slot t holds l1 = brev(pos0 + t)).
+// MODE 0: times w_j, then the first inverse (DIT) group on the same slots.
+// MODE 1: |X|^2 in FP64 into row `row` of the A tile, at natural l1.
+template <typename V, int NT, int NB, int MODE, typename K>
+__device__ __forceinline__ void phc_row_mid(const K& k) {
+    typedef typename VT<V>::R Rt;
+    constexpr int P = 1 << NB;
+    const int items = k.RW() << (k.lg1() - NB);
+    for (int it = threadIdx.x; it < items; it += NT) {
+        const int row = it & (k.RW() - 1), g = it >> k.lgRW();
+        const int pos0 = g << NB;
+        V* rb = k.B + row * k.LDB();
+        V v[P];
+#pragma unroll
+        for (int t = 0; t < P; ++t) v[t] = rb[pos0 + t];
+        phc_small_dif<V, NB, false>(v);
+        if constexpr (MODE == 1) {
+            double* q = reinterpret_cast<double*>(k.A) + row * k.LDB();
+#pragma unroll
+            for (int t = 0; t < P; ++t)
+                q[brev(pos0 + t, k.lg1())] = (double)v[t].x * v[t].x + (double)v[t].y * v[t].y;
+        } else {
+            const Rt* wr = k.W + row * k.LDB();
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                const Rt ww = wr[brev(pos0 + t, k.lg1())];
+                v[t].x *= ww;
+                v[t].y *= ww;
+            }
+            phc_small_dit<V, NB, true>(v);
+#pragma unroll
+            for (int t = 0; t < P; ++t) rb[pos0 + t] = v[t];
+        }
+    }
+}
+
+// Row phase, inverse (DIT over l1), group gi >= 1 (the stages of forward group
+// ng - 1 - gi, on the same slot sets).
+template <typename V, int NT, int NB, typename K>
+__device__ __forceinline__ void phc_row_inv(const K& k, int gi) {
+    constexpr int P = 1 << NB;
+    const int hb = phc_ghb(k.lg1(), phc_ngroups(k.lg1()) - 1 - gi);
+    const int items = k.RW() << (k.lg1() - NB);
+    for (int it = threadIdx.x; it < items; it += NT) {
+        const int row = it & (k.RW() - 1), g = it >> k.lgRW();
+        const int pos0 = phc_pos0<NB>(g, hb);
+        V* rb = k.B + row * k.LDB();
+        V v[P];
+#pragma unroll
+        for (int t = 0; t < P; ++t) v[t] = rb[pos0 | (t << hb)];
+        phc_dit<V, NB, true>(v, hb, g & ((1 << hb) - 1), k.twf, k.lg1());
+#pragma unroll
+        for (int t = 0; t < P; ++t) rb[pos0 | (t << hb)] = v[t];
+    }
+}
+
+// Column phase, inverse (DIF over l2, conjugate roots), group gi.  The first
+// group applies exp(+2 pi i l2 m1 / n); the last writes conj(psi_j) .* W*(...)
+// (+ sC x for mask 0) to plane j and adds Re<x, plane> to the thread's sum.
+template <typename V, int NT, int NB, int DOT, typename K>
+__device__ __forceinline__ void phc_col_inv(const K& k, const KP<V>& p, const V* __restrict__ x, V* __restrict__ out,
+                                            int gi, bool first, bool last, CompSum<typename VT<V>::R>& acc) {
+    typedef typename VT<V>::R Rt;
+    constexpr int P = 1 << NB;
+    const int hb = phc_ghb(k.lg2(), gi);
+    const int items = k.CW() << (k.lg2() - NB);
+    const V* __restrict__ mask = p.masks + (size_t)k.j * k.n;
+    V* __restrict__ plane = out + (size_t)k.j * p.ldb;
+    const Rt sC = (Rt)p.c.sC;
+    for (int it = threadIdx.x; it < items; it += NT) {
+        const int c = it & (k.CW() - 1), g = it >> k.lgCW();
+        const int pos0 = phc_pos0<NB>(g, hb);
+        V v[P], mk[P], xe[P];
+        if (K::kFixed && last) {   // hb == 0: slot t will hold m2 = brev(pos0 + t)
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                const int e = k.c0() + c + brev(pos0 + t, k.lg2()) * k.n1();
+                mk[t] = mask[e];
+                xe[t] = x[e];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            const int pos = pos0 | (t << hb);
+            v[t] = k.A[pos * k.LDA() + c];
+            if (first) v[t] = CX<V>::cmul(p.tw4[(size_t)pos * k.n1() + k.c0() + c], v[t]);
+        }
+        phc_dif<V, NB, true>(v, hb, g & ((1 << hb) - 1), k.twf, k.lg1());
+        if (last) {
+#pragma unroll
+            for (int t = 0; t < P; ++t) {
+                const int e = k.c0() + c + brev(pos0 + t, k.lg2()) * k.n1();
+                if (!K::kFixed) {
+                    mk[t] = mask[e];
+                    xe[t] = x[e];
+                }
+                V val = CX<V>::cmul(mk[t], v[t]);
+                if (k.j == 0) {
+                    val.x += sC * xe[t].x;
+                    val.y += sC * xe[t].y;
+                }
+                plane[e] = val;
+                if (DOT) {
+                    acc.add(xe[t].x, val.x);
+                    acc.add(xe[t].y, val.y);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < P; ++t) k.A[(pos0 | (t << hb)) * k.LDA() + c] = v[t];
+        }
+    }
+}
+
+// MODE 0: D-matvec planes (out + j ldb, mask j) of x with weights w (internal
+// order); DOT: also Re<x, D x> and the end of Lanczos step i.
+// MODE 1: the primal update of the iteration from the Ritz vector (Eq. 6.2:
+// z <- (1 - eta) z + eta A(alpha v v*) / ||v||^2 with A(v v*)_j = |W(psi_j v)|^2),
+// the sketch update and the dual step size (as k_ph_p2<1>).
+// LG1 > 0: the shape n1 = 2^LG1, n2 = 2^LG2, C = 2^LGC is compiled in.
+template <typename V, int NT, int MODE, int DOT, int LG1, int LG2, int LGC>
+__global__ void __launch_bounds__(NT, 1) k_phc(KP<V> p, const V* __restrict__ x,
+                                               const typename VT<V>::R* __restrict__ w, V* __restrict__ out, int i) {
+    typedef typename VT<V>::R Rt;
+    typedef PhcK<V, LG1, LG2, LGC> K;
+    constexpr int MAXG = 3;   // groups per transform (lg <= 12)
+    // with the shape compiled in, the first column group has exactly one work item per thread
+    static_assert(LG1 == 0 || (1 << (LG1 + LG2 - LGC - phc_gsize(LG2, 0))) == NT, "one item per thread");
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    K k;
+    k.lg1r = p.log1;
+    k.lg2r = p.log2;
+    k.lgCr = __ffs((int)cl.num_blocks()) - 1;
+    k.n = 1 << (k.lg1() + k.lg2());
+    k.r = (int)cl.block_rank();
+    k.j = blockIdx.x >> k.lgC();
+    const PhcGeom gm = phc_geom(k.n1(), k.n2(), 1 << k.lgC(), (int)sizeof(V));
+    k.A = reinterpret_cast<V*>(smraw);
+    k.B = reinterpret_cast<V*>(smraw + gm.offB);
+    k.W = reinterpret_cast<Rt*>(smraw + gm.offW);
+    k.twf = reinterpret_cast<V*>(smraw + gm.offT);
+    k.A32 = (uint32_t)__cvta_generic_to_shared(k.A);
+    k.B32 = (uint32_t)__cvta_generic_to_shared(k.B);
+    // the roots of unity (first copy group; they never change, so the copy starts
+    // before the wait for the preceding kernel) and this block's rows of w_j
+    // (second group; internal order, so contiguous), copied asynchronously: w is
+    // waited for only at the first cluster barrier
+    for (int t = threadIdx.x; t < k.n1(); t += NT) phc_cp_async<(int)sizeof(V)>(k.twf + t, p.twiddle + (t << k.lg2()));
+    phc_cp_commit();
+    pdl_wait();
+    // the flag does not change during the launch, so either every block returns or none does
+    if (MODE == 1 && p.sc->converged) {
+        phc_cp_wait_all();
+        return;
+    }
+    if constexpr (MODE == 0) {
+        const Rt* __restrict__ wj = w + (size_t)k.j * k.n + ((size_t)k.l0() << k.lg1());
+        for (int idx = threadIdx.x; idx < (k.RW() << k.lg1()); idx += NT)
+            phc_cp_async<(int)sizeof(Rt)>(k.W + (idx >> k.lg1()) * k.LDB() + (idx & (k.n1() - 1)), wj + idx);
+    }
+    phc_cp_commit();
+    if constexpr (!K::kFixed) {   // else the first column group waits once its loads are in flight
+        phc_cp_wait_group<1>();
+        __syncthreads();
+    }
+    const int ng2 = phc_ngroups(k.lg2()), ng1 = phc_ngroups(k.lg1());
+    const V* __restrict__ xin = (MODE == 1) ? p.vbuf : x;
+#pragma unroll
+    for (int gi = 0; gi < MAXG; ++gi) {
+        if (gi < ng2) {
+            phc_nb(phc_gsize(k.lg2(), gi), [&](auto nbc) {
+                phc_col_fwd<V, NT, decltype(nbc)::value>(k, p, xin, gi, gi == 0, gi == ng2 - 1);
+            });
+            if (gi < ng2 - 1) __syncthreads();
+        }
+    }
+    phc_cp_wait_all();
+    cl.sync();   // B tiles and w complete; every block is done reading its A tile
+#pragma unroll
+    for (int gi = 0; gi < MAXG - 1; ++gi) {
+        if (gi < ng1 - 1) {
+            phc_nb(phc_gsize(k.lg1(), gi), [&](auto nbc) { phc_row_fwd<V, NT, decltype(nbc)::value>(k, gi); });
+            __syncthreads();
+        }
+    }
+    phc_nb(phc_gsize(k.lg1(), ng1 - 1), [&](auto nbc) { phc_row_mid<V, NT, decltype(nbc)::value, MODE>(k); });
+    if constexpr (MODE == 0) {
+#pragma unroll
+        for (int gi = 1; gi < MAXG; ++gi) {
+            if (gi < ng1) {
+                __syncthreads();
+                phc_nb(phc_gsize(k.lg1(), ng1 - 1 - gi), [&](auto nbc) {
+                    phc_row_inv<V, NT, decltype(nbc)::value>(k, gi);
+                });
+            }
+        }
+        __syncthreads();
+        phc_push_rows<V, NT>(k);
+        cl.sync();   // A tiles complete; no shared-memory access crosses blocks after this
+        CompSum<Rt> acc;
+#pragma unroll
+        for (int gi = 0; gi < MAXG; ++gi) {
+            if (gi < ng2) {
+                phc_nb(phc_gsize(k.lg2(), gi), [&](auto nbc) {
+                    phc_col_inv<V, NT, decltype(nbc)::value, DOT>(k, p, x, out, gi, gi == 0, gi == ng2 - 1, acc);
+                });
+                if (gi < ng2 - 1) __syncthreads();
+            }
+        }
+        if constexpr (DOT != 0) {
+            double v[1] = {acc.total()};
+            __shared__ double tot[1];
+            if (grid_reduce<1, double, NT>(v, p.partials, p.ticket, tot)) finish_lanczos_step<V, NT>(p, i, tot[0]);
+        }
+    } else {
+        __syncthreads();
+        DevScalars* sc = p.sc;
+        const double eta = sc->eta, nv2 = sc->nv2;
+        const int take = sc->take_h;
+        const double zc = take ? eta * p.c.alpha * p.c.sA / nv2 : 0.0;
+        const double betap = p.c.beta0 * sqrt((double)(sc->t + 2));   // beta_{t+1}: wbar of Alg. D.1
+        const double* q = reinterpret_cast<const double*>(k.A);
+        const size_t base = (size_t)k.j * k.n + ((size_t)k.l0() << k.lg1());
+        double a_nzb = 0.0, a_yzb = 0.0, a_yy = 0.0;
+        for (int idx = threadIdx.x; idx < (k.RW() << k.lg1()); idx += NT) {
+            const size_t ii = base + idx;
+            const double a2 = q[(idx >> k.lg1()) * k.LDB() + (idx & (k.n1() - 1))];
+            const double zi = fma(1.0 - eta, p.z[ii], zc * a2);
+            p.z[ii] = zi;
+            const double zb = zi - (p.c.kleq ? fmin(zi + p.y[ii] / betap, p.b[ii]) : p.b[ii]);
+            a_nzb = fma(zb, zb, a_nzb);
+            if (p.c.K_finite) {
+                const double yi = p.y[ii];
+                a_yzb = fma(yi, zb, a_yzb);
+                a_yy = fma(yi, yi, a_yy);
+            }
+        }
+        // sketch update S <- (1 - eta) S + eta alpha v (v* Omega) / ||v||^2 (grid-stride over n R)
+        const int R = p.c.R;
+        __shared__ V rr[SCGAL_RMAX];
+        if (threadIdx.x < R) {
+            rr[threadIdx.x].x = (Rt)sc->r[2 * threadIdx.x];
+            rr[threadIdx.x].y = (Rt)sc->r[2 * threadIdx.x + 1];
+        }
+        __syncthreads();
+        const Rt sfac = take ? (Rt)(eta * p.c.alpha / nv2) : (Rt)0;
+        const Rt om1 = (Rt)(1.0 - eta);
+        const long long nR = (long long)k.n * R;
+        for (long long e2 = (long long)blockIdx.x * NT + threadIdx.x; e2 < nR; e2 += (long long)gridDim.x * NT) {
+            const int e = (int)(e2 / R);
+            const int c = (int)(e2 - (long long)e * R);
+            const V vr = CX<V>::mul(p.vbuf[e], rr[c]);
+            V sv = p.S[e2];
+            sv.x = om1 * sv.x + sfac * vr.x;
+            sv.y = om1 * sv.y + sfac * vr.y;
+            p.S[e2] = sv;
+        }
+        double red[3] = {a_nzb, a_yzb, a_yy};
+        __shared__ double tot[3];
+        if (grid_reduce<3, double, NT>(red, p.partials, p.ticket, tot))
+            if (threadIdx.x == 0) phase_update_finish(p, tot);
+    }
+}
+
+template <typename V> constexpr int phc_threads() { return sizeof(V) == 8 ? 512 : 256; }
 
 // ---------------------------------------------------------------------------
 // transform tile, then the length-n2 (columns) or length-n1 (rows) twiddles
@@ -573,27 +1167,8 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_update(KP<V> p) {
     }
     double red[3] = {a_nzb, a_yzb, a_yy};
     __shared__ double tot[3];
-    if (grid_reduce<3>(red, p.partials, p.ticket, tot)) {
-        if (threadIdx.x == 0) {
-            const Consts& c = p.c;
-            sc->vCv = c.sC;
-            sc->p = (1.0 - eta) * sc->p + (take ? eta * c.alpha * c.sC : 0.0);
-            sc->tau = (1.0 - eta) * sc->tau + (take ? eta * c.alpha : 0.0);
-            const double nzb2 = tot[0];
-            const long long t = sc->t;
-            double gamma = (nzb2 == 0.0)
-                               ? c.beta0
-                               : fmin(c.beta0, 4.0 * c.alpha * c.alpha * c.beta0 * c.normA_s * c.normA_s /
-                                                   (pow((double)(t + 1), 1.5) * nzb2));
-            if (c.K_finite) {
-                const double yy = tot[2] + 2.0 * gamma * tot[1] + gamma * gamma * nzb2;
-                if (sqrt(yy) > c.K) gamma = 0.0;
-            }
-            sc->gamma = gamma;
-            sc->nzb2_new = nzb2;
-            p.hist[(t - 1) % c.hist_cap].gamma = gamma;
-        }
-    }
+    if (grid_reduce<3>(red, p.partials, p.ticket, tot))
+        if (threadIdx.x == 0) phase_update_finish(p, tot);
 }
 
 template <typename V> int prepare_fp_kernels(const KP<V>& p) {
@@ -621,6 +1196,87 @@ template <typename V> int prepare_phase_kernels(const KP<V>& p) {
     return SCGAL_OK;
 }
 
+// Blocks per cluster for a length-2^log2n transform: the smallest power of two
+// that leaves at most 8192 (FP32) or 4096 (FP64) points per block, if that is
+// at most 16 and the short side (n2 = 2^floor(log2n / 2)) has at least 16
+// points; 0 otherwise (only the three-pass kernels run).
+template <typename V> int phase_cluster_size(int log2n) {
+    const int lg2 = log2n / 2;
+    if (lg2 < 4) return 0;
+    const int cap_lg = (sizeof(V) == 8) ? 13 : 12;
+    const int lgC = std::max(0, log2n - cap_lg);
+    if (lgC > 4 || lgC > lg2) return 0;
+    return 1 << lgC;
+}
+
+// The instantiation for the handle's shape: FP32 n = 2^16 (C = 8) and
+// n = 2^17 (C = 16) compiled in, every other shape read at run time.
+template <typename V, int MODE, int DOT, typename F>
+static auto phc_pick(const KP<V>& p, F&& f) {
+    constexpr int NT = phc_threads<V>();
+    if constexpr (sizeof(V) == 8) {
+        if (p.log2n == 16 && p.phC == 8) return f(k_phc<V, NT, MODE, DOT, 8, 8, 3>);
+        if (p.log2n == 17 && p.phC == 16) return f(k_phc<V, NT, MODE, DOT, 9, 8, 4>);
+    }
+    return f(k_phc<V, NT, MODE, DOT, 0, 0, 0>);
+}
+
+// Launch shape: C * L blocks in clusters of C (and, with pdl, programmatic
+// dependent launch); `at` holds two attributes.
+static cudaLaunchConfig_t phc_config(int C, int L, int nt, size_t smem, cudaStream_t s, cudaLaunchAttribute* at,
+                                     bool pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C * L);
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 2 : 1;
+    return cfg;
+}
+
+template <typename V, int MODE, int DOT>
+static cudaError_t launch_phc(const KP<V>& p, const V* x, const typename VT<V>::R* w, V* out, int i, cudaStream_t s) {
+    const PhcGeom g = phc_geom(p.n1, p.n2, p.phC, (int)sizeof(V));
+    cudaLaunchAttribute at[2];
+    const cudaLaunchConfig_t cfg = phc_config(p.phC, p.c.L, phc_threads<V>(), g.bytes, s, at, true);
+    return phc_pick<V, MODE, DOT>(p, [&](auto kern) { return cudaLaunchKernelEx(&cfg, kern, p, x, w, out, i); });
+}
+
+template <typename V, int MODE, int DOT>
+static cudaError_t phc_attrs(const KP<V>& p, int L, int* clusters) {
+    const PhcGeom g = phc_geom(p.n1, p.n2, p.phC, (int)sizeof(V));
+    return phc_pick<V, MODE, DOT>(p, [&](auto kern) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.bytes);
+        if (e == cudaSuccess && p.phC > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess || !clusters) return e;
+        cudaLaunchAttribute at[2];
+        const cudaLaunchConfig_t cfg = phc_config(p.phC, L, phc_threads<V>(), g.bytes, nullptr, at, false);
+        return cudaOccupancyMaxActiveClusters(clusters, kern, &cfg);
+    });
+}
+
+// Sets the clustered kernels' shared-memory and cluster-size attributes and
+// returns how many clusters fit on the device at once (0 or negative: they
+// cannot run, and the three-pass kernels must).
+template <typename V> int prepare_phase_cluster(const KP<V>& p, int L) {
+    int nc = 0;
+    cudaError_t e = phc_attrs<V, 0, 0>(p, L, nullptr);
+    if (e == cudaSuccess) e = phc_attrs<V, 0, 1>(p, L, nullptr);
+    if (e == cudaSuccess) e = phc_attrs<V, 1, 0>(p, L, &nc);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return nc;
+}
+
 template <typename V> void launch_phase_step(const KP<V>& p, int i, cudaStream_t s) {
     const V* x = p.basis + (size_t)i * p.ldb;
     if (p.c.kind == KIND_PTYCHO) {
@@ -628,7 +1284,11 @@ template <typename V> void launch_phase_step(const KP<V>& p, int i, cudaStream_t
         k_fp_gather<V, 1><<<p.fpGrid, SCGAL_BS, 0, s>>>(p, x, p.ybuf, i);
         return;
     }
-    // the column and row passes skip nothing on breakdown; only their cost is wasted
+    // the passes skip nothing on breakdown; only their cost is wasted
+    if (p.phC) {
+        launch_phc<V, 0, 1>(p, x, p.wvec, p.ybuf, i, s);
+        return;
+    }
     forward_and_weight<V>(p, x, p.wvec, s);
     k_ph_p3<V, 1><<<dim3(p.n1 / p.ph_tc, p.ynplanes), SCGAL_BS, col_smem(p), s>>>(p, x, p.ybuf, i);
 }
@@ -637,6 +1297,10 @@ template <typename V> void launch_phase_update(const KP<V>& p, int grid, cudaStr
     (void)grid;
     if (p.c.kind == KIND_PTYCHO) {
         k_fp_update<V><<<p.c.L, SCGAL_BS, fp_smem(p), s>>>(p);
+        return;
+    }
+    if (p.phC) {
+        launch_phc<V, 1, 0>(p, nullptr, nullptr, nullptr, 0, s);
         return;
     }
     k_ph_p1<V><<<dim3(p.n1 / p.ph_tc, p.c.L), SCGAL_BS, col_smem(p), s>>>(p, p.vbuf);
@@ -650,8 +1314,12 @@ void launch_apply_D_phase(const KP<V>& p, const V* x, V* out, const typename VT<
         k_fp_gather<V, 0><<<p.fpGrid, SCGAL_BS, 0, s>>>(p, x, out, 0);
         return;
     }
-    forward_and_weight<V>(p, x, w, s);
-    k_ph_p3<V, 0><<<dim3(p.n1 / p.ph_tc, p.ynplanes), SCGAL_BS, col_smem(p), s>>>(p, x, p.ybuf, 0);
+    if (p.phC) {
+        launch_phc<V, 0, 0>(p, x, w, p.ybuf, 0, s);
+    } else {
+        forward_and_weight<V>(p, x, w, s);
+        k_ph_p3<V, 0><<<dim3(p.n1 / p.ph_tc, p.ynplanes), SCGAL_BS, col_smem(p), s>>>(p, x, p.ybuf, 0);
+    }
     k_plane_sum<V><<<(p.c.n + 255) / 256, 256, 0, s>>>(p.ybuf, p.ynplanes, p.ldb, p.c.n, out);
 }
 
@@ -680,6 +1348,8 @@ void phase_perm(const double* in, double* out, long long d, int n, int n1, int n
 #define INST(V)                                                                                           \
     template int prepare_phase_kernels<V>(const KP<V>&);                                                  \
     template int prepare_fp_kernels<V>(const KP<V>&);                                                     \
+    template int prepare_phase_cluster<V>(const KP<V>&, int);                                             \
+    template int phase_cluster_size<V>(int);                                                              \
     template void launch_phase_step<V>(const KP<V>&, int, cudaStream_t);                                  \
     template void launch_phase_update<V>(const KP<V>&, int, cudaStream_t);                                \
     template void launch_apply_D_phase<V>(const KP<V>&, const V*, V*, const typename VT<V>::R*, cudaStream_t); \

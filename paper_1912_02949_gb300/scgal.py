@@ -28,6 +28,7 @@ SCGAL_LMO_EQ, SCGAL_LMO_LEQ, SCGAL_LMO_DEFAULT = 0, 1, -1
 SCGAL_OMEGA_STORED, SCGAL_OMEGA_REGEN = 0, 1
 SCGAL_K_EQ, SCGAL_K_LEQ = 0, 1
 SCGAL_SPMV_AUTO, SCGAL_SPMV_GATHER, SCGAL_SPMV_TILED = 0, 1, 2
+SCGAL_FFT_AUTO, SCGAL_FFT_PASSES, SCGAL_FFT_CLUSTER = 0, 1, 2
 
 
 class ScgalError(RuntimeError):
@@ -40,7 +41,7 @@ class scgal_params(Structure):
     _fields_ = [("R", c_int32), ("T_max", c_int32), ("tol", c_double), ("beta0", c_double), ("K", c_double),
                 ("lmo", c_int32), ("scale", c_int32), ("trace_correct", c_int32), ("precision", c_int32),
                 ("seed", c_uint64), ("instance", c_uint32), ("check_every", c_int32), ("device", c_int32),
-                ("omega", c_int32), ("kset", c_int32), ("tune", c_int32), ("spmv", c_int32)]
+                ("omega", c_int32), ("kset", c_int32), ("tune", c_int32), ("spmv", c_int32), ("fft", c_int32)]
 
 
 class scgal_stats(Structure):
@@ -57,7 +58,8 @@ class scgal_info(Structure):
                 ("lmo", c_int32), ("trace_correct", c_int32), ("scale", c_int32), ("nnz", c_int64),
                 ("weight_kind", c_int32), ("qmax", c_int32), ("t", c_int64), ("alpha", c_double),
                 ("normC", c_double), ("normA", c_double), ("device_bytes", c_int64), ("spmv_group", c_int32),
-                ("spmv_grid", c_int32), ("spmv_kind", c_int32), ("tiled_slots", c_int64)]
+                ("spmv_grid", c_int32), ("spmv_kind", c_int32), ("tiled_slots", c_int64),
+                ("fft_cluster", c_int32)]
 
 
 class scgal_result(Structure):
