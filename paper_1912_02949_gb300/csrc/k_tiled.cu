@@ -9,10 +9,12 @@
 // columns.  Tile (J, SG) holds the stored entries (r, c) with r in super-group
 // SG and c in column block J; tiles are stored column-block-major (tile
 // J * NSG + SG), so the entries of one column block form one contiguous range.
-// Inside a tile the entries are sorted by row (CSR order within a row) and
-// packed four to a group -- the unit one lane of pass 2 takes -- such that a
-// row's entries never straddle two groups unless it has more than four
-// entries in the tile.  Each slot holds
+// Inside a tile a row's entries are consecutive (CSR order) and packed four
+// to a group -- the unit one lane of pass 2 takes -- such that they never
+// straddle two groups unless the row has more than four entries in the tile;
+// rows with one entry in the tile fill the remaining slots so that the rows
+// a warp adds at once fall in distinct shared-memory banks where they can
+// (arrange_tile).  Each slot holds
 //   c16: column - J CB (15 bits) | the sign of a +-1 weight << 15,
 //   r16: row - SG SR (13 bits) | CONT (same row as the slot before it in the
 //        group) | END (last slot of its row's run in the group: the run's sum
@@ -419,19 +421,107 @@ void bucket_super_group(int SG, const TiledGeom& g, int n, const int* rp, const 
         }
 }
 
-// Slots of one tile after packing runs into groups of four.
-uint32_t packed_size(const int* rows, size_t m) {
+// Slot of every entry of one tile (rows[0..m) sorted, a row's entries
+// consecutive); returns the tile's slot count (a multiple of four).  Runs of
+// two or more entries keep their row order and are packed as they come (a run
+// of at most four never crosses a group of four; longer runs span groups).
+// Single-entry runs -- most of them on sparse graphs -- then fill the free
+// slots so that, within each block of 128 slots (one pass-2 warp step: 32
+// lanes x 4 slot columns), the rows whose runs END in the same slot column
+// fall in distinct shared-memory banks (row mod 32) wherever the counts allow:
+// pass 2 adds each column's 32 runs with one shared-memory read-modify-write
+// across the warp.  Deterministic: the same graph always gives the same layout.
+uint32_t arrange_tile(const int* rows, size_t m, std::vector<int>& slot) {
+    slot.assign(m, -1);
+    std::vector<int> occ;   // row of each slot, -1 when free
+    std::vector<int> singles;
     uint32_t pos = 0;
     size_t k = 0;
     while (k < m) {
         size_t f = k;
         while (f < m && rows[f] == rows[k]) ++f;
         const uint32_t len = (uint32_t)(f - k);
-        if (len <= 4 && (pos & 3u) + len > 4) pos = (pos + 3u) & ~3u;
-        pos += len;
+        if (len == 1) {
+            singles.push_back((int)k);
+        } else {
+            if (len <= 4 && (pos & 3u) + len > 4) pos = (pos + 3u) & ~3u;
+            if (occ.size() < pos + len) occ.resize(pos + len, -1);
+            for (uint32_t u = 0; u < len; ++u) {
+                slot[k + u] = (int)(pos + u);
+                occ[pos + u] = rows[k];
+            }
+            pos += len;
+        }
         k = f;
     }
-    return (pos + 3u) & ~3u;
+    const size_t used = occ.size();
+    size_t free_in = 0;
+    for (size_t q = 0; q < used; ++q) free_in += occ[q] < 0;
+    const size_t total = used + (singles.size() > free_in ? singles.size() - free_in : 0);
+    const uint32_t size = (uint32_t)((total + 3) & ~(size_t)3);
+    occ.resize(size, -1);
+    // singles by bank, each list in row order
+    std::vector<int> bank_list[32];
+    for (int e : singles) bank_list[rows[e] & 31].push_back(e);
+    size_t head[32] = {0};
+    size_t left = singles.size();
+    std::vector<uint32_t> free_pos[4];
+    for (uint32_t b0 = 0; b0 < size && left > 0; b0 += 128) {
+        const uint32_t b1 = std::min<uint32_t>(size, b0 + 128);
+        // free slots of each column of this block, and the banks the END slots of
+        // longer runs already take there
+        unsigned taken[4] = {0u, 0u, 0u, 0u};
+        for (int c = 0; c < 4; ++c) free_pos[c].clear();
+        for (uint32_t q = b0; q < b1; ++q) {
+            if (occ[q] < 0) {
+                free_pos[q & 3u].push_back(q);
+                continue;
+            }
+            const bool end = ((q & 3u) == 3u) || q + 1 >= size || occ[q + 1] != occ[q];
+            if (end) taken[q & 3u] |= 1u << (occ[q] & 31);
+        }
+        size_t cap[4], nfree = 0;
+        for (int c = 0; c < 4; ++c) nfree += (cap[c] = free_pos[c].size());
+        // how many singles of each bank this block takes: one per bank in turn,
+        // the banks with the most singles left first
+        size_t need = std::min(nfree, left), cnt[32] = {0};
+        int order[32];
+        for (int bk = 0; bk < 32; ++bk) order[bk] = bk;
+        std::stable_sort(order, order + 32, [&](int x, int y) {
+            return bank_list[x].size() - head[x] > bank_list[y].size() - head[y];
+        });
+        while (need > 0)
+            for (int u = 0; u < 32 && need > 0; ++u) {
+                const int bk = order[u];
+                if (bank_list[bk].size() - head[bk] > cnt[bk]) {
+                    ++cnt[bk];
+                    --need;
+                }
+            }
+        // columns for each bank's singles, largest counts first, each into the
+        // column with the most free slots that does not hold the bank yet
+        std::stable_sort(order, order + 32, [&](int x, int y) { return cnt[x] > cnt[y]; });
+        size_t fill[4] = {0, 0, 0, 0};
+        for (int u = 0; u < 32; ++u) {
+            const int bk = order[u];
+            for (size_t c = 0; c < cnt[bk]; ++c) {
+                int best = -1;
+                for (int pass = 0; pass < 2 && best < 0; ++pass)
+                    for (int col = 0; col < 4; ++col) {
+                        if (cap[col] == 0 || (pass == 0 && (taken[col] & (1u << bk)))) continue;
+                        if (best < 0 || cap[col] > cap[best]) best = col;
+                    }
+                const int e = bank_list[bk][head[bk]++];
+                const uint32_t q = free_pos[best][fill[best]++];
+                slot[(size_t)e] = (int)q;
+                occ[q] = rows[e];
+                taken[best] |= 1u << bk;
+                --cap[best];
+                --left;
+            }
+        }
+    }
+    return size;
 }
 
 template <typename F>
@@ -457,13 +547,13 @@ int tiled_build(int n, const int* rp, const int* col, const R* val, const TiledG
                 std::vector<uint16_t>& c16, std::vector<uint16_t>& r16, std::vector<R>& tval) {
     const size_t nt = (size_t)g.NJ * g.NSG;
     std::vector<uint32_t> size(nt, 0);
-    // pass A: packed size of every tile
+    // pass A: slot count of every tile
     parallel_for(g.NSG, [&](int SG) {
-        std::vector<int> idx, row, start;
+        std::vector<int> idx, row, start, slot;
         bucket_super_group(SG, g, n, rp, col, idx, row, start);
         for (int J = 0; J < g.NJ; ++J)
             size[(size_t)J * g.NSG + SG] =
-                packed_size(row.data() + start[J], (size_t)(start[J + 1] - start[J]));
+                arrange_tile(row.data() + start[J], (size_t)(start[J + 1] - start[J]), slot);
     });
     tseg.assign(nt + 1, 0);
     unsigned long long acc = 0;
@@ -478,27 +568,21 @@ int tiled_build(int n, const int* rp, const int* col, const R* val, const TiledG
     if (val) tval.assign(acc, (R)0);
     // pass B: slots and run codes
     parallel_for(g.NSG, [&](int SG) {
-        std::vector<int> idx, row, start;
+        std::vector<int> idx, row, start, slot;
         std::vector<uint16_t> raw;
         bucket_super_group(SG, g, n, rp, col, idx, row, start);
         for (int J = 0; J < g.NJ; ++J) {
             const size_t A = tseg[(size_t)J * g.NSG + SG];
             const size_t B = A + size[(size_t)J * g.NSG + SG];
-            size_t pos = A;
-            int k = start[J];
-            while (k < start[J + 1]) {
-                int f = k;
-                while (f < start[J + 1] && row[(size_t)f] == row[(size_t)k]) ++f;
-                const size_t len = (size_t)(f - k);
-                if (len <= 4 && ((pos - A) & 3u) + len > 4) pos = A + (((pos - A) + 3u) & ~(size_t)3u);
-                for (int m = k; m < f; ++m, ++pos) {
-                    const int e = idx[(size_t)m];
-                    const int c = col[e] & 0x7fffffff;
-                    c16[pos] = (uint16_t)((c - J * g.CB) | (col[e] < 0 ? 0x8000 : 0));
-                    r16[pos] = (uint16_t)(row[(size_t)m] - SG * g.SR);
-                    if (val) tval[pos] = val[e];
-                }
-                k = f;
+            const int k0 = start[J];
+            arrange_tile(row.data() + k0, (size_t)(start[J + 1] - k0), slot);
+            for (int m = k0; m < start[J + 1]; ++m) {
+                const size_t pos = A + (size_t)slot[(size_t)(m - k0)];
+                const int e = idx[(size_t)m];
+                const int c = col[e] & 0x7fffffff;
+                c16[pos] = (uint16_t)((c - J * g.CB) | (col[e] < 0 ? 0x8000 : 0));
+                r16[pos] = (uint16_t)(row[(size_t)m] - SG * g.SR);
+                if (val) tval[pos] = val[e];
             }
             // run codes (raw rows are < 8192, padding is PAD_ROW)
             raw.assign(r16.begin() + A, r16.begin() + B);
