@@ -273,12 +273,14 @@ int scgal_get_info(scgal_t h, scgal_info* out);
 
 /* Measurement: launch one of the iteration's kernels `reps` times back to back
  * on the handle's stream between two CUDA events and report the mean duration
- * of one launch in milliseconds.  kernel: 0 the Lanczos D-matvec step (MaxCut:
- * CSR pass fused with the omega reduction; phase retrieval: the three FFT
- * passes), 1 the three-term update, 2 the Ritz vector, 3 the tridiagonal
- * eigensolver.  Works on the iteration t the handle is about to run, with
- * private scalars: the solver state is unchanged (only per-iteration scratch
- * is overwritten), so call it between iterations. */
+ * of one launch in milliseconds.  kernel: 0 the first Lanczos D-matvec step
+ * (MaxCut: the CSR kernel with the omega reduction, or the two tiled passes;
+ * phase retrieval: the FFT kernel(s)), 1 the three-term update as a launch of
+ * its own, 2 the Ritz vector, 3 the tridiagonal eigensolver, 4 one Lanczos
+ * step as the solver runs it (D-matvec and three-term update in sequence):
+ * the mean over the q steps of about reps / q whole Lanczos runs.  Works on the iteration t the handle
+ * is about to run, with private scalars: the solver state is unchanged (only
+ * per-iteration scratch is overwritten), so call it between iterations. */
 int scgal_time_kernel(scgal_t h, int32_t kernel, int32_t reps, double* ms_per_launch);
 
 /* Allocation-free D-matvec with its inner product.  The paper has no

@@ -94,14 +94,21 @@ constexpr int TUNE_DEFAULT_CAP = 6;
 template <typename V> int tune_spmv_grid(scgal_ctx* h);
 
 // ---------------------------------------------------------------------------
+// The q Lanczos steps of Alg. 4.1: the D-matvec with omega, then the
+// three-term update between steps.
 template <typename V>
-void enqueue_iteration(scgal_ctx* h, int q, cudaStream_t s) {
-    KP<V>& p = kp<V>(h);
+void enqueue_lanczos_run(scgal_ctx* h, const KP<V>& p, int q, cudaStream_t s) {
     for (int i = 0; i < q; ++i) {
         if constexpr (VT<V>::cplx) launch_phase_step<V>(p, i, s);
         else launch_spmv_step<V>(p, h->grid_spmv, h->spmv_group, i, s);
         if (i < q - 1) launch_lanczos_update<V>(p, h->grid_elem, i, s);
     }
+}
+
+template <typename V>
+void enqueue_iteration(scgal_ctx* h, int q, cudaStream_t s) {
+    KP<V>& p = kp<V>(h);
+    enqueue_lanczos_run<V>(h, p, q, s);
     launch_tridiag<V>(p, q, s);
     launch_ritz<V>(p, h->grid_ritz, s);
     if constexpr (VT<V>::cplx) launch_phase_update<V>(p, h->grid_elem, s);
@@ -153,7 +160,7 @@ int setup_state(scgal_ctx* h) {
     if (!h->c.omega_regen) ALLOC(h, om, sizeof(V) * (size_t)n * R);   // else regenerated at each use
     p.Omega = om;
     ALLOC(h, p.S, sizeof(V) * (size_t)n * R);
-    const int gmax = std::max(std::max(h->grid_elem, h->grid_spmv), p.tiled ? p.tNSG : 0);
+    const int gmax = std::max(std::max(h->grid_elem, h->grid_spmv), p.tiled ? std::max(p.tNSG, p.tNJ * p.tS) : 0);
     ALLOC(h, p.partials, sizeof(double) * (size_t)gmax * (1 + 2 * SCGAL_RMAX));
     ALLOC(h, p.ticket, sizeof(unsigned) * 4);
     ALLOC(h, p.sc, sizeof(DevScalars));
@@ -1064,11 +1071,7 @@ int do_lanczos(scgal_ctx* h, const double* w, long long t, int q, double* xi, in
     }
     CUDA_TRY(h, cudaMemsetAsync(a.sc, 0, sizeof(DevScalars), s));
     launch_start_only<V>(p, h->grid_elem, t, s);
-    for (int i = 0; i < q; ++i) {
-        if constexpr (VT<V>::cplx) launch_phase_step<V>(p, i, s);
-        else launch_spmv_step<V>(p, h->grid_spmv, h->spmv_group, i, s);
-        if (i < q - 1) launch_lanczos_update<V>(p, h->grid_elem, i, s);
-    }
+    enqueue_lanczos_run<V>(h, p, q, s);
     launch_tridiag<V>(p, q, s);
     launch_ritz<V>(p, h->grid_ritz, s);
     DevScalars hs;
@@ -1104,18 +1107,34 @@ int do_time_kernel(scgal_ctx* h, int kernel, int reps, double* ms) {
     };
     CUDA_TRY(h, cudaMemsetAsync(a.sc, 0, sizeof(DevScalars), s));
     launch_start_only<V>(p, h->grid_elem, t, s);
-    if (kernel >= 2) {   // a full Lanczos run first, so T and the basis are q deep
-        for (int i = 0; i < q; ++i) {
-            step(i);
-            if (i < q - 1) launch_lanczos_update<V>(p, h->grid_elem, i, s);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(h, cudaEventCreate(&e0));
+    CUDA_TRY(h, cudaEventCreate(&e1));
+    if (kernel == 4) {   // whole Lanczos runs: mean time of a step (with its update) over q steps
+        double tot = 0.0;
+        const int runs = std::max(1, reps / std::max(1, q));
+        for (int r = 0; r < runs; ++r) {
+            launch_start_only<V>(p, h->grid_elem, t, s);
+            CUDA_TRY(h, cudaEventRecord(e0, s));
+            enqueue_lanczos_run<V>(h, p, q, s);
+            CUDA_TRY(h, cudaEventRecord(e1, s));
+            CUDA_TRY(h, cudaEventSynchronize(e1));
+            float el = 0.f;
+            cudaEventElapsedTime(&el, e0, e1);
+            tot += el;
         }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        CUDA_TRY(h, cudaGetLastError());
+        *ms = tot / runs / q;
+        return SCGAL_OK;
+    }
+    if (kernel >= 2) {   // a full Lanczos run first, so T and the basis are q deep
+        enqueue_lanczos_run<V>(h, p, q, s);
         launch_tridiag<V>(p, q, s);
     } else if (kernel == 1) {
         step(0);
     }
-    cudaEvent_t e0, e1;
-    CUDA_TRY(h, cudaEventCreate(&e0));
-    CUDA_TRY(h, cudaEventCreate(&e1));
     CUDA_TRY(h, cudaEventRecord(e0, s));
     for (int r = 0; r < reps; ++r) {
         if (kernel == 0) step(0);
@@ -1558,7 +1577,7 @@ int scgal_lanczos(scgal_t h, const double* w, int64_t t, int32_t q, double* xi, 
 }
 
 int scgal_time_kernel(scgal_t h, int32_t kernel, int32_t reps, double* ms_per_launch) {
-    if (!h || !ms_per_launch || kernel < 0 || kernel > 3 || reps < 1) return SCGAL_EINVAL;
+    if (!h || !ms_per_launch || kernel < 0 || kernel > 4 || reps < 1) return SCGAL_EINVAL;
     if (h->sticky) return h->sticky;
     DeviceGuard guard(h);
     return DISPATCH(h, do_time_kernel, h, kernel, reps, ms_per_launch);

@@ -219,6 +219,29 @@ template <> struct CompSum<float> {
 };
 
 // --------------------------------------------------------------------------
+// This thread's share of a block-strided sum: s + x[t] + x[t + BS] + ... (in
+// that order, t = threadIdx.x, indices below m), read through L2.  Eight loads
+// are issued before any is added, so a block sums m partials in about
+// m / (8 BS) L2 round trips instead of m / BS; the additions keep their order,
+// so the result is the same as the one-at-a-time loop's.
+template <int BS>
+__device__ __forceinline__ double strided_sum_cg(const double* __restrict__ x, int m, double s = 0.0) {
+    constexpr int U = 8;
+    for (int b0 = threadIdx.x; b0 < m; b0 += U * BS) {
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int b = b0 + u * BS;
+            v[u] = b < m ? __ldcg(x + b) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (b0 + u * BS < m) s += v[u];
+    }
+    return s;
+}
+
+// --------------------------------------------------------------------------
 // Deterministic grid reduction of NV doubles (blockDim.x == BS, a multiple of
 // 32; 1-D or 2-D grids, blocks numbered blockIdx.y * gridDim.x + blockIdx.x).
 // Returns true in exactly one block (the last to arrive); there tot[0..NV)
@@ -259,7 +282,7 @@ __device__ __forceinline__ bool grid_reduce(WT (&v)[NV], double* __restrict__ pa
     // fixed-order sum of the partials
     for (int k = 0; k < NV; ++k) {
         double s = 0.0;
-        for (unsigned b = threadIdx.x; b < nblk; b += BS) s += __ldcg(&partials[(size_t)k * nblk + b]);
+        s = strided_sum_cg<BS>(partials + (size_t)k * nblk, (int)nblk, s);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) red[wid][0] = s;
@@ -302,7 +325,7 @@ __device__ __forceinline__ double block_sum_array(const double* x, int m) {
     __shared__ double res;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double s = 0.0;
-    for (int b = threadIdx.x; b < m; b += BS) s += __ldcg(x + b);
+    s = strided_sum_cg<BS>(x, m, s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) red[wid] = s;

@@ -346,9 +346,8 @@ __global__ void __launch_bounds__(W * 32, W == 4 ? 7 : 4) k_tile_rows(KP<V> p, i
         if (!last) return;
         __threadfence();
         double s1 = 0.0, s2 = 0.0;
-        for (int b = threadIdx.x; b < NSG; b += W * 32) s1 += __ldcg(p.partials + b);
-        if (i > 0)
-            for (int b = threadIdx.x; b < p.nupd; b += W * 32) s2 += __ldcg(p.upart + b);
+        s1 = strided_sum_cg<W * 32>(p.partials, NSG, s1);
+        if (i > 0) s2 = strided_sum_cg<W * 32>(p.upart, p.nupd, s2);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             s1 += __shfl_down_sync(0xffffffffu, s1, o);
