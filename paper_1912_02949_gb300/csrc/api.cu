@@ -170,7 +170,8 @@ int setup_state(scgal_ctx* h) {
     ALLOC(h, p.coef, sizeof(double) * (h->qmax + 2));
     ALLOC(h, p.hist, sizeof(scgal_stats) * (size_t)hist_cap);
     p.nupd = update_grid<V>(n);   // blocks of every Lanczos update launch (one partial each)
-    ALLOC(h, p.upart, sizeof(double) * (size_t)std::max(gmax, p.nupd));
+    p.upcap = std::max(gmax, p.nupd);
+    ALLOC(h, p.upart, sizeof(double) * 2 * (size_t)p.upcap);   // two buffers (step parity)
     {
         int* qt = nullptr;
         ALLOC(h, qt, sizeof(int) * (size_t)h->prm.T_max);
@@ -513,6 +514,7 @@ int phase_build(scgal_ctx* h, const double* masks, const double* b) {
             return set_err(h, SCGAL_EINVAL, "the transform does not fit the clustered D-matvec kernel");
     }
     if (p.phC) p.ynplanes = L;   // one output plane per mask
+    p.fin_upd = 1;               // the update ends each step (few partials)
     h->phase_cluster = p.phC;
     Consts& c = h->c;
     c.kind = KIND_PHASE;
@@ -799,6 +801,7 @@ int ptycho_build(scgal_ctx* h, const double* pupil, const double* b, int M, int 
     p.b = db;
     p.fpcov = dcov;
     p.ynplanes = 1;
+    p.fin_upd = 1;               // the update ends each step (few partials)
     h->grid_elem = grid_for(d, SCGAL_BS, 4);
     p.fpGrid = std::min(grid_for(n, SCGAL_BS, 4), h->grid_elem);
     h->grid_spmv = std::max(h->grid_elem, L);   // the update kernel reduces over L blocks

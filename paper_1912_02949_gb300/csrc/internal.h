@@ -111,8 +111,12 @@ struct KP {
     double* sv;         // 1 / ||w_i|| of raw basis vector i
     double* coef;       // Ritz coefficients u_j * sv_j
     scgal_stats* hist;
-    double* upart;      // per-block partial ||W_{i+1}||^2 of the last Lanczos update
-    int nupd;           // blocks of the Lanczos update kernel (entries of upart)
+    double* upart;      // per-block partial ||W_{i+1}||^2 of the Lanczos updates, two buffers of upcap
+    int nupd;           // blocks of the Lanczos update kernel (partials per buffer)
+    int upcap;          // entries of one upart buffer
+    int fin_upd;        // 1: a step's <W_i, D W_i> partials are added up, and the step ended, by the
+                        // update that follows (and the tridiagonal solve after the last step);
+                        // 0: by the step kernel's last block (grid ticket)
     const int* qtab;    // q_t for t = 1..T_max (computed on the host)
     // tiled MaxCut D-matvec (k_tiled.cu): tiles (J, SG) of tSR rows x tCB columns,
     // stored column-block-major (tile J * tNSG + SG); every slot holds one stored
@@ -126,45 +130,142 @@ struct KP {
     typename VT<V>::R* tprod;          // per-slot products of the current D-matvec
 };
 
-// End of a Lanczos D-matvec step i, thread 0 of the last block only: from
-// rr = ||W_i||^2 (the previous update's per-block partials, summed) rho_{i-1},
-// the breakdown test of Alg. 4.1 (exact rho == 0), the scale s_i = 1 / rho_{i-1},
-// and omega_i = s_i^2 <W_i, D W_i> from dot = <W_i, D W_i>.  Nothing is recorded
-// once the iteration has converged or broken down.
+// End of a Lanczos D-matvec step i, from rr = ||W_i||^2 and dot = <W_i, D W_i>:
+// rho_{i-1} = sqrt(rr), the breakdown test of Alg. 4.1 (exact rho == 0), the
+// scale s_i = 1 / rho_{i-1}, and omega_i = s_i^2 dot.
+struct StepScalars {
+    double rho, s, om;
+};
+template <typename V>
+__device__ __forceinline__ StepScalars step_scalars(const KP<V>& p, int i, double dot, double rr) {
+    StepScalars r;
+    r.rho = (i > 0) ? sqrt(rr) : 0.0;
+    r.s = (i > 0) ? 1.0 / r.rho : p.sv[0];
+    r.om = r.s * r.s * dot;
+    return r;
+}
+
+// Records the end of step i (one thread): omega_i, rho_{i-1}, s_i and the
+// Lanczos length k = i + 1 -- nothing once the iteration has converged or broken
+// down; a zero rho stops the run (T is i x i), a non-finite one or a
+// non-finite omega is a numerical failure.
 template <typename V>
 __device__ __forceinline__ void finish_lanczos_scalars(const KP<V>& p, int i, double dot, double rr) {
     DevScalars* sc = p.sc;
     if (sc->converged || sc->stop) return;
+    const StepScalars st = step_scalars(p, i, dot, rr);
     if (i > 0) {
-        const double rho = sqrt(rr);
-        if (rho == 0.0) {           // invariant subspace found: T is i x i
+        if (st.rho == 0.0) {        // invariant subspace found: T is i x i
             sc->stop = 1;
             return;
         }
-        if (!isfinite(rho)) {
+        if (!isfinite(st.rho)) {
             sc->stop = 1;
             sc->err = SCGAL_ENUMERIC;
             sc->converged = 1;
             return;
         }
-        p.rh[i - 1] = rho;
-        p.sv[i] = 1.0 / rho;
+        p.rh[i - 1] = st.rho;
+        p.sv[i] = st.s;
     }
-    const double si = p.sv[i];
-    const double om = si * si * dot;
-    if (!isfinite(om)) {
+    if (!isfinite(st.om)) {
         sc->err = SCGAL_ENUMERIC;
         sc->converged = 1;
     }
-    p.om[i] = om;
+    p.om[i] = st.om;
     sc->k = i + 1;
 }
 
-// The same for a last block of BS threads (all of them call it).
+// A D-matvec step's share of <W_i, D W_i>: the block's threads' values added in
+// a fixed order, written to partials[block] (flattened 2-D block index); block 0
+// also records the number of partials in ticket[2].  No grid-wide wait: the
+// kernel that follows (the update, or the tridiagonal solve after the last
+// step) adds the partials up (step_sums) and finishes the step.
+template <int BS>
+__device__ __forceinline__ void write_step_partial(double* partials, unsigned* ticket, double v) {
+    __shared__ double red[BS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < BS / 32; ++w) t += red[w];
+        const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+        partials[bid] = t;
+        if (bid == 0) ticket[2] = gridDim.x * gridDim.y;
+    }
+}
+
+// The end of step i in the step kernel's last block (p.fin_upd == 0): the
+// previous update's ||W_i||^2 partials added up here; every thread of that
+// block (BS of them) calls it.
 template <typename V, int BS = SCGAL_BS>
+__device__ __forceinline__ void finish_lanczos_step(const KP<V>& p, int i, double dot);
+
+// The ||W||^2 partials of the update that formed W_i, for the end of step i
+// (double-buffered by step parity: the update of step i reads one buffer while
+// it writes the other).
+template <typename V>
+__device__ __forceinline__ double* upart_of(const KP<V>& p, int i) {
+    return p.upart + (size_t)(i & 1) * p.upcap;
+}
+
+template <typename V, int BS>
 __device__ __forceinline__ void finish_lanczos_step(const KP<V>& p, int i, double dot) {
-    const double rr = (i > 0) ? block_sum_array<BS>(p.upart, p.nupd) : 0.0;
+    const double rr = (i > 0) ? block_sum_array<BS>(upart_of(p, i), p.nupd) : 0.0;
     if (threadIdx.x == 0) finish_lanczos_scalars(p, i, dot, rr);
+}
+
+// A step kernel's <W_i, D W_i>: with p.fin_upd its block partial (the update
+// ends the step), else the grid reduction whose last block ends the step.
+template <typename V, int BS>
+__device__ __forceinline__ void step_dot(const KP<V>& p, int i, double v) {
+    if (p.fin_upd) {
+        write_step_partial<BS>(p.partials, p.ticket, v);
+    } else {
+        double a[1] = {v};
+        __shared__ double tot[1];
+        if (grid_reduce<1, double, BS>(a, p.partials, p.ticket, tot)) finish_lanczos_step<V, BS>(p, i, tot[0]);
+    }
+}
+
+// Every thread of a block of BS threads receives dot = sum of the step's
+// partials and rr = ||W_i||^2 (the previous update's partials), each added in
+// the same fixed order in every block.
+template <typename V, int BS>
+__device__ __forceinline__ void step_sums(const KP<V>& p, int i, double& dot, double& rr) {
+    __shared__ double r1[BS / 32], r2[BS / 32];
+    __shared__ double res[2];
+    const int nd = (int)__ldcg(p.ticket + 2);
+    double s1 = strided_sum_cg<BS>(p.partials, nd);
+    double s2 = (i > 0) ? strided_sum_cg<BS>(upart_of(p, i), p.nupd) : 0.0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+        r1[wid] = s1;
+        r2[wid] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+#pragma unroll
+        for (int w = 0; w < BS / 32; ++w) {
+            a += r1[w];
+            b += r2[w];
+        }
+        res[0] = a;
+        res[1] = b;
+    }
+    __syncthreads();
+    dot = res[0];
+    rr = res[1];
 }
 
 }  // namespace scgal

@@ -104,11 +104,17 @@ __global__ void __launch_bounds__(SCGAL_BS) k_dual_start(KP<V> p, int do_dual) {
 }
 
 // ---------------------------------------------------------------------------
-// The update is linear with real coefficients, so it runs on the real view of
-// the vectors (2n reals for complex ones) with 16-byte loads.  It has no grid
-// reduction: each block leaves its partial ||W_{i+1}||^2 in upart, and the next
-// D-matvec step adds them up (finish_lanczos_step).  Speculative like that step:
-// after a breakdown sv[i] may be stale, and the row it writes is never read.
+// With p.fin_upd the update first ends step i: every block adds up the step's
+// <W_i, D W_i> partials and the previous update's ||W_i||^2 partials in the
+// same fixed order (step_sums), so all blocks derive the same s_i, omega_i,
+// rho_{i-1}, and block 0 records them (finish_lanczos_scalars); cheap for the
+// phase-retrieval steps' few partials, while the MaxCut steps' many partials
+// read by every block of a large update grid would crowd the L2 lines holding
+// them, so there the step kernel's last block ends the step.  The recurrence is linear
+// with real coefficients, so it runs on the real view of the vectors (2n reals
+// for complex ones) with 16-byte loads; each block leaves its partial
+// ||W_{i+1}||^2 in the other upart buffer for the end of step i+1.
+// Speculative: after a breakdown the row it writes is never read.
 template <typename V>
 __global__ void __launch_bounds__(SCGAL_BS, 4) k_lanczos_update(KP<V> p, int i) {
     typedef typename VT<V>::R Rt;
@@ -116,10 +122,23 @@ __global__ void __launch_bounds__(SCGAL_BS, 4) k_lanczos_update(KP<V> p, int i) 
     constexpr int UN = 2;              // 16-byte groups per thread in flight
     struct alignas(16) RV { Rt v[W]; };
     pdl_wait();
-    const double si = p.sv[i];
+    double si, om, rho;
+    if (p.fin_upd) {   // end step i here (see above); else its last block did
+        double dot, rr;
+        step_sums<V, SCGAL_BS>(p, i, dot, rr);
+        if (blockIdx.x == 0 && threadIdx.x == 0) finish_lanczos_scalars(p, i, dot, rr);
+        const StepScalars ss = step_scalars(p, i, dot, rr);
+        si = ss.s;
+        om = ss.om;
+        rho = ss.rho;
+    } else {
+        si = p.sv[i];
+        om = p.om[i];
+        rho = (i > 0) ? p.rh[i - 1] : 0.0;
+    }
     const Rt a = (Rt)si;
-    const Rt b = (Rt)(-p.om[i] * si);
-    const Rt c = (i > 0) ? (Rt)(-p.rh[i - 1] * p.sv[i - 1]) : (Rt)0;
+    const Rt b = (Rt)(-om * si);
+    const Rt c = (i > 0) ? (Rt)(-rho * p.sv[i - 1]) : (Rt)0;
     constexpr int CF = VT<V>::cplx ? 2 : 1;
     const long long m = (long long)p.c.n * CF;        // reals per vector
     const long long ldr = p.ldb * CF;                  // reals between basis rows (multiple of 64)
@@ -168,12 +187,20 @@ __global__ void __launch_bounds__(SCGAL_BS, 4) k_lanczos_update(KP<V> p, int i) 
         Wn[k] = w;
         acc.add(w, w);
     }
-    block_sum_to<double>(acc.total(), p.upart + blockIdx.x);
+    block_sum_to<double>(acc.total(), upart_of(p, i + 1) + blockIdx.x);
 }
 
+// With p.fin_upd, ends the run's last step (q - 1, no update follows it); then
+// the tridiagonal eigenpair.
 template <typename V>
 __global__ void __launch_bounds__(SCGAL_BS) k_tridiag(KP<V> p, int q) {
     pdl_wait();
+    if (p.fin_upd) {
+        double dot, rr;
+        step_sums<V, SCGAL_BS>(p, q - 1, dot, rr);
+        if (threadIdx.x == 0) finish_lanczos_scalars(p, q - 1, dot, rr);
+        __syncthreads();
+    }
     if (p.sc->converged) return;
     extern __shared__ double smt[];
     tridiag_body<V>(p, q, smt);

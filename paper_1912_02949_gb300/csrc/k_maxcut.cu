@@ -116,16 +116,13 @@ __device__ __forceinline__ double spmv_chunks(const KP<V>& p, const V* __restric
     return dot.total();
 }
 
-// Lanczos step i: Y = D W_i and omega_i = s_i^2 <W_i, Y>.
-// Runs speculatively: it writes only per-iteration scratch (ybuf) until its last
-// block, which records omega_i (and rho_{i-1} from the previous update) only if
-// the iteration is live -- so no warp waits on the flags before its first load.
+// Lanczos step i: Y = D W_i and <W_i, Y>, from which the step's end records
+// omega_i = s_i^2 <W_i, Y> (step_dot).  Writes only per-iteration scratch, so
+// it runs without looking at the flags.
 template <typename V, int WK>
 __global__ void __launch_bounds__(SCGAL_BS) k_spmv_step(KP<V> p, int i) {
     const V* x = p.basis + (size_t)i * p.ldb;
-    double v[1] = {spmv_chunks<V, WK>(p, x, p.ybuf, p.dvec)};
-    __shared__ double tot[1];
-    if (grid_reduce<1, double>(v, p.partials, p.ticket, tot)) finish_lanczos_step(p, i, tot[0]);
+    step_dot<V, SCGAL_BS>(p, i, spmv_chunks<V, WK>(p, x, p.ybuf, p.dvec));
 }
 
 // After the Ritz vector: v* C v (primitive (1), one more CSR pass), the primal

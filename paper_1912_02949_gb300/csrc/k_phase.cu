@@ -317,11 +317,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ph_p3(KP<V> p, const V* __restrict
             if (DOT) dot += xe.x * val.x + xe.y * val.y;
         }
     }
-    if constexpr (DOT) {
-        double v[1] = {(double)dot};
-        __shared__ double tot[1];
-        if (grid_reduce_2d<1>(v, p.partials, p.ticket, tot)) finish_lanczos_step(p, i, tot[0]);
-    }
+    if constexpr (DOT) step_dot<V, SCGAL_BS>(p, i, (double)dot);
 }
 
 template <typename V>
@@ -881,11 +877,7 @@ __global__ void __launch_bounds__(NT, 1) k_phc(KP<V> p, const V* __restrict__ x,
                 if (gi < ng2 - 1) __syncthreads();
             }
         }
-        if constexpr (DOT != 0) {
-            double v[1] = {acc.total()};
-            __shared__ double tot[1];
-            if (grid_reduce<1, double, NT>(v, p.partials, p.ticket, tot)) finish_lanczos_step<V, NT>(p, i, tot[0]);
-        }
+        if constexpr (DOT != 0) step_dot<V, NT>(p, i, acc.total());
     } else {
         __syncthreads();
         DevScalars* sc = p.sc;
@@ -1102,11 +1094,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_gather(KP<V> p, const V* __rest
         out[e] = val;
         if (DOT) dot += xe.x * val.x + xe.y * val.y;
     }
-    if constexpr (DOT) {
-        double v[1] = {(double)dot};
-        __shared__ double tot[1];
-        if (grid_reduce<1>(v, p.partials, p.ticket, tot)) finish_lanczos_step(p, i, tot[0]);
-    }
+    if constexpr (DOT) step_dot<V, SCGAL_BS>(p, i, (double)dot);
 }
 
 // Primal update of the iteration (Eq. 6.2): z <- (1 - eta) z + eta A(alpha v v*)

@@ -36,8 +36,9 @@
 // The Lanczos-step form of pass 2 also reduces <x, D x>: FP64 in the FP64
 // path; in the FP32 path each lane accumulates its rows' products without
 // rounding error in a pair of floats (the product split exactly by one FMA,
-// the sum carried by the two-sum rule), and lanes, warps and blocks are added
-// in FP64.  The last block then finishes the step (omega_i, rho_{i-1}).
+// the sum carried by the two-sum rule), and lanes and warps are added in FP64
+// into one partial per super-group, and the step is ended (omega_i,
+// rho_{i-1}) as step_dot arranges.
 #include <algorithm>
 #include <thread>
 #include <vector>
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(TP_BS) k_tile_products(KP<V> p, const V* __res
 
 // ---------------------------------------------------------------------------
 // Pass 2: rows of super-group SG.  STEP: the Lanczos step i (x = W_i, out =
-// ybuf, diag = dvec, <x, D x> reduced and the step finished in the last block).
+// ybuf, diag = dvec, and this super-group's share of <x, D x>).
 // Seven 4-warp CTAs fit an SM, so the 1024 super-groups of n = 2^20 run in one wave.
 template <typename V, int W, bool STEP>
 __global__ void __launch_bounds__(W * 32, W == 4 ? 7 : 4) k_tile_rows(KP<V> p, int i, const V* __restrict__ x, V* __restrict__ out,
@@ -325,51 +326,7 @@ __global__ void __launch_bounds__(W * 32, W == 4 ? 7 : 4) k_tile_rows(KP<V> p, i
             }
         }
     }
-    if constexpr (STEP) {
-        // fixed-order reduction over lanes, warps and blocks; the last block finishes
-        __shared__ double wsum[W];
-        __shared__ bool last;
-        double d = dacc.total();
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-        if (lane == 0) wsum[wid] = d;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-#pragma unroll
-            for (int w2 = 0; w2 < W; ++w2) t += wsum[w2];
-            p.partials[SG] = t;
-            __threadfence();
-            last = atomicAdd(p.ticket, 1u) == (unsigned)NSG - 1u;
-        }
-        __syncthreads();
-        if (!last) return;
-        __threadfence();
-        double s1 = 0.0, s2 = 0.0;
-        s1 = strided_sum_cg<W * 32>(p.partials, NSG, s1);
-        if (i > 0) s2 = strided_sum_cg<W * 32>(p.upart, p.nupd, s2);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s1 += __shfl_down_sync(0xffffffffu, s1, o);
-            s2 += __shfl_down_sync(0xffffffffu, s2, o);
-        }
-        __shared__ double w1[W], w2s[W];
-        if (lane == 0) {
-            w1[wid] = s1;
-            w2s[wid] = s2;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double dot = 0.0, rr = 0.0;
-#pragma unroll
-            for (int w2 = 0; w2 < W; ++w2) {
-                dot += w1[w2];
-                rr += w2s[w2];
-            }
-            *p.ticket = 0u;
-            finish_lanczos_scalars(p, i, dot, rr);
-        }
-    }
+    if constexpr (STEP) step_dot<V, W * 32>(p, i, dacc.total());
 }
 
 // ---------------------------------------------------------------------------
