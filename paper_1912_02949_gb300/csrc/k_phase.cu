@@ -1041,6 +1041,141 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_apply(KP<V> p, const V* __restr
     }
 }
 
+// ---------------------------------------------------------------------------
+// k_fp_apply for M = 64 (the benchmark's windows): the same window operator
+// with the radix-8 groups of the clustered four-step kernel (phc_small_dif /
+// phc_small_dit / phc_twiddle).  The conjugate 2-D DFT runs decimation in
+// frequency (rows, then columns: natural in, bit-reversed out), w_j is applied
+// at the bit-reversed positions, and the 2-D DFT runs decimation in time
+// (columns, then rows: bit-reversed in, natural out), so no pass permutes
+// data.  Row passes put lanes across rows and column passes across columns;
+// the tile's row stride M + 1 keeps both free of bank conflicts.  Each pass
+// is a group of three radix-2 stages in registers (two groups per length-64
+// transform); the last column group of the first transform, the weight and
+// the first column group of the second run as one pass.
+template <typename V>
+__global__ void __launch_bounds__(SCGAL_BS) k_fp_apply64(KP<V> p, const V* __restrict__ x,
+                                                         const typename VT<V>::R* __restrict__ w) {
+    typedef typename VT<V>::R Rt;
+    constexpr int LG = 6, M = 1 << LG, LD = M + 1, NB = 3, P = 1 << NB, m = M * M;
+    constexpr int ITEMS = M * (M / P);   // work items of a pass (512)
+    extern __shared__ unsigned char smraw[];
+    V* a = reinterpret_cast<V*>(smraw);
+    V* twf = a + (size_t)M * LD;        // exp(-2 pi i k / M), k < M
+    const int N = p.fpN;
+    const int j = blockIdx.x;
+    const int kr = j / p.fpK, kc = j - kr * p.fpK;
+    const int r0 = kr * p.fpS, c0 = kc * p.fpS;   // < N
+    for (int k = threadIdx.x; k < M; k += SCGAL_BS) twf[k] = p.twiddle[k];
+    // pupil .* the window of x, natural order (eight loads in flight per thread)
+    constexpr int UL = 8;
+    for (int base = threadIdx.x; base < m; base += SCGAL_BS * UL) {
+        V xv[UL], pv[UL];
+#pragma unroll
+        for (int u = 0; u < UL; ++u) {
+            const int idx = base + u * SCGAL_BS;
+            const int r = idx >> LG, c = idx & (M - 1);
+            int gr = r0 + r;
+            if (gr >= N) gr -= N;
+            int gc = c0 + c;
+            if (gc >= N) gc -= N;
+            xv[u] = x[(size_t)gr * N + gc];
+            pv[u] = p.masks[idx];
+        }
+#pragma unroll
+        for (int u = 0; u < UL; ++u) {
+            const int idx = base + u * SCGAL_BS;
+            a[(idx >> LG) * LD + (idx & (M - 1))] = CX<V>::mul(pv[u], xv[u]);
+        }
+    }
+    __syncthreads();
+    // rows, conjugate DFT (DIF): group 0 (column bits 3..5), group 1 (bits 0..2)
+#pragma unroll
+    for (int grp = 0; grp < 2; ++grp) {
+        const int hb = grp == 0 ? 3 : 0;
+        for (int it = threadIdx.x; it < ITEMS; it += SCGAL_BS) {
+            const int row = it & (M - 1), g = it >> LG;
+            const int pos0 = grp == 0 ? g : g << NB;
+            V* rb = a + row * LD;
+            V v[P];
+#pragma unroll
+            for (int t = 0; t < P; ++t) v[t] = rb[pos0 | (t << hb)];
+            phc_dif<V, NB, true>(v, hb, g & ((1 << hb) - 1), twf, LG);
+#pragma unroll
+            for (int t = 0; t < P; ++t) rb[pos0 | (t << hb)] = v[t];
+        }
+        __syncthreads();
+    }
+    // columns, conjugate DFT (DIF) group 0
+    for (int it = threadIdx.x; it < ITEMS; it += SCGAL_BS) {
+        const int col = it & (M - 1), g = it >> LG;
+        V v[P];
+#pragma unroll
+        for (int t = 0; t < P; ++t) v[t] = a[(g | (t << 3)) * LD + col];
+        phc_dif<V, NB, true>(v, 3, g, twf, LG);
+#pragma unroll
+        for (int t = 0; t < P; ++t) a[(g | (t << 3)) * LD + col] = v[t];
+    }
+    __syncthreads();
+    // columns: DIF group 1 (rows now at bit-reversed positions), times w_j at the
+    // natural frequency (brev(row position), brev(column position)), then the
+    // forward DFT's first DIT group on the same slots
+    const Rt* __restrict__ wj = w + (size_t)j * m;
+    for (int it = threadIdx.x; it < ITEMS; it += SCGAL_BS) {
+        const int col = it & (M - 1), g = it >> LG;
+        const int pos0 = g << NB;
+        const int cn = brev(col, LG);
+        V v[P];
+        Rt wv[P];
+#pragma unroll
+        for (int t = 0; t < P; ++t) wv[t] = wj[brev(pos0 + t, LG) * M + cn];
+#pragma unroll
+        for (int t = 0; t < P; ++t) v[t] = a[(pos0 + t) * LD + col];
+        phc_small_dif<V, NB, true>(v);
+#pragma unroll
+        for (int t = 0; t < P; ++t) {
+            v[t].x *= wv[t];
+            v[t].y *= wv[t];
+        }
+        phc_small_dit<V, NB, false>(v);
+#pragma unroll
+        for (int t = 0; t < P; ++t) a[(pos0 + t) * LD + col] = v[t];
+    }
+    __syncthreads();
+    // columns: forward DIT group 1 (row bits 3..5): natural row order
+    for (int it = threadIdx.x; it < ITEMS; it += SCGAL_BS) {
+        const int col = it & (M - 1), g = it >> LG;
+        V v[P];
+#pragma unroll
+        for (int t = 0; t < P; ++t) v[t] = a[(g | (t << 3)) * LD + col];
+        phc_dit<V, NB, false>(v, 3, g, twf, LG);
+#pragma unroll
+        for (int t = 0; t < P; ++t) a[(g | (t << 3)) * LD + col] = v[t];
+    }
+    __syncthreads();
+    // rows: forward DIT groups 0 (column bits 0..2) and 1 (bits 3..5): natural columns
+#pragma unroll
+    for (int grp = 0; grp < 2; ++grp) {
+        const int hb = grp == 0 ? 0 : 3;
+        for (int it = threadIdx.x; it < ITEMS; it += SCGAL_BS) {
+            const int row = it & (M - 1), g = it >> LG;
+            const int pos0 = grp == 0 ? g << NB : g;
+            V* rb = a + row * LD;
+            V v[P];
+#pragma unroll
+            for (int t = 0; t < P; ++t) v[t] = rb[pos0 | (t << hb)];
+            phc_dit<V, NB, false>(v, hb, g & ((1 << hb) - 1), twf, LG);
+#pragma unroll
+            for (int t = 0; t < P; ++t) rb[pos0 | (t << hb)] = v[t];
+        }
+        __syncthreads();
+    }
+    // times conj(pupil), into the window's slice of fftbuf (coalesced)
+    V* out = p.fftbuf + (size_t)j * m;
+    for (int idx = threadIdx.x; idx < m; idx += SCGAL_BS)
+        out[idx] = CX<V>::cmul(p.masks[idx], a[(idx >> LG) * LD + (idx & (M - 1))]);
+}
+
 // out = sC x + (sum over the windows covering each pixel); DOT: also reduce
 // Re<x, D x> and finish Lanczos step i.
 template <typename V, int DOT>
@@ -1159,9 +1294,20 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_update(KP<V> p) {
         if (threadIdx.x == 0) phase_update_finish(p, tot);
 }
 
+// Shared memory of k_fp_apply64: one M x (M + 1) tile and the M roots.
+template <typename V> static size_t fp64_smem() { return sizeof(V) * (64 * 65 + 64); }
+
+template <typename V>
+static void launch_fp_apply(const KP<V>& p, const V* x, const typename VT<V>::R* w, cudaStream_t s) {
+    if (p.fpM == 64) k_fp_apply64<V><<<p.c.L, SCGAL_BS, fp64_smem<V>(), s>>>(p, x, w);
+    else k_fp_apply<V><<<p.c.L, SCGAL_BS, fp_smem(p), s>>>(p, x, w);
+}
+
 template <typename V> int prepare_fp_kernels(const KP<V>& p) {
     const int sm = (int)fp_smem(p);
     cudaError_t e = cudaFuncSetAttribute(k_fp_apply<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fp_apply64<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp64_smem<V>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fp_update<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1268,7 +1414,7 @@ template <typename V> int prepare_phase_cluster(const KP<V>& p, int L) {
 template <typename V> void launch_phase_step(const KP<V>& p, int i, cudaStream_t s) {
     const V* x = p.basis + (size_t)i * p.ldb;
     if (p.c.kind == KIND_PTYCHO) {
-        k_fp_apply<V><<<p.c.L, SCGAL_BS, fp_smem(p), s>>>(p, x, p.wvec);
+        launch_fp_apply<V>(p, x, p.wvec, s);
         k_fp_gather<V, 1><<<p.fpGrid, SCGAL_BS, 0, s>>>(p, x, p.ybuf, i);
         return;
     }
@@ -1298,7 +1444,7 @@ template <typename V> void launch_phase_update(const KP<V>& p, int grid, cudaStr
 template <typename V>
 void launch_apply_D_phase(const KP<V>& p, const V* x, V* out, const typename VT<V>::R* w, cudaStream_t s) {
     if (p.c.kind == KIND_PTYCHO) {
-        k_fp_apply<V><<<p.c.L, SCGAL_BS, fp_smem(p), s>>>(p, x, w);
+        launch_fp_apply<V>(p, x, w, s);
         k_fp_gather<V, 0><<<p.fpGrid, SCGAL_BS, 0, s>>>(p, x, out, 0);
         return;
     }
