@@ -126,6 +126,18 @@ typedef struct {
                                by the phase-retrieval problems */
     int32_t  fft;           /* SCGAL_FFT_*: coded-diffraction D-matvec kernel (default AUTO);
                                ignored by the other problems */
+    int32_t  keep_state;    /* serving (scgal_submit, MaxCut): 1 keeps the request's final iterate
+                               (z, y, sketch S, p, tau, t) in the server's host memory when it
+                               finishes, for later requests' warm_from (at most 1 GB is kept;
+                               the oldest states are dropped first); ignored elsewhere */
+    int64_t  warm_from;     /* serving (scgal_submit, MaxCut): ticket of a finished request submitted
+                               with keep_state, on a graph with the same n (a neighbouring instance:
+                               edges added, removed or reweighted) and the same R and precision.
+                               The request starts from that iterate -- z, y, S, p and tau as they
+                               were, the iteration counter t at a quarter of its final value, so
+                               the step sizes of Alg. 6.1 (eta = 2 / (t + 1)) let the new graph's
+                               directions in -- instead of from zero (Section 6.2's state); 0: cold.
+                               A missing or mismatched source is a cold start */
 } scgal_params;
 
 /* One iteration record (Alg. 6.1 step t; stopping values of Eq. E.1 for the
@@ -337,13 +349,14 @@ const char* scgal_strerror(int status);
 typedef struct {
     int32_t  status;        /* SCGAL_OK converged, SCGAL_ENOTDONE hit T_max, < 0 error */
     int32_t  n;
-    int64_t  iterations;    /* iterations whose update was applied */
+    int64_t  iterations;    /* iterations whose update was applied (from first_t on) */
     double   relgap, infeas;
     double   objective;     /* <C, X> original units (MaxCut: -SDP value estimate) */
     int64_t  best_cut;      /* rounded cut weight (Section 7.2.1) */
     double   lambda_max;    /* largest eigenvalue of the reconstruction */
     double   queue_ms;      /* submit -> admission */
     double   latency_ms;    /* submit -> result ready */
+    int64_t  first_t;       /* the iteration the solve started at: 1, or the warm start's t */
 } scgal_result;
 
 typedef struct {

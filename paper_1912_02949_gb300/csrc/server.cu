@@ -15,6 +15,10 @@
 //      rounding, result published for scgal_poll, device memory released;
 //   4. waits for the round and marks the solves that finished in it.
 // A request that arrives while others are mid-solve joins at the next round.
+// Warm starts: a request submitted with keep_state leaves its final iterate in
+// host memory; a later request on a graph of the same size that names it in
+// warm_from starts from that iterate (Section 6.2's state: z, y, the sketch,
+// p and tau) with the iteration counter at a quarter of its final value.
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -47,6 +51,15 @@ struct Request {
     scgal_params prm{};
     double t_submit = 0, t_admit = 0;
     size_t footprint = 0;
+    long long first_t = 1;              // 1, or the iteration a warm start resumed at
+};
+
+// Final iterate of a finished request submitted with keep_state (host copies).
+struct Saved {
+    int n = 0, R = 0, prec = 0;
+    std::vector<double> z, y, S;
+    double sc[4] = {0, 0, 0, 0};        // p, tau, t, converged (scgal_get_state)
+    size_t bytes() const { return sizeof(double) * (z.size() + y.size() + S.size()); }
 };
 
 struct Slot {
@@ -117,6 +130,11 @@ struct scgal_server {
     static constexpr int CHUNK = 8;          // iterations per graph-path slot per round
     static constexpr unsigned long long BATCH_BUDGET_NS = 25000000ull;   // batched launch time per round
     static constexpr size_t QUEUE_MAX = 1 << 16;
+    // iterates kept for warm starts (keep_state requests), oldest dropped past the cap
+    std::map<uint64_t, Saved> saved;
+    std::deque<uint64_t> saved_order;
+    size_t saved_bytes = 0;
+    static constexpr size_t SAVED_CAP = size_t(1) << 30;
     // batched engine state (device arrays owned by the worker thread)
     cudaStream_t bstream = nullptr;
     char* d_slots = nullptr;
@@ -171,6 +189,46 @@ struct scgal_server {
         if (st) s.fin_st = *st;
     }
 
+    // The finished solve's iterate, kept for warm starts (oldest dropped past the cap).
+    void keep(Slot& s) {
+        Saved v;
+        v.n = s.req.n;
+        v.R = s.req.prm.R;
+        v.prec = s.req.prm.precision;
+        v.z.resize((size_t)s.req.n);
+        v.y.resize((size_t)s.req.n);
+        v.S.resize((size_t)s.req.n * s.req.prm.R);
+        if (scgal_get_state(s.h, v.z.data(), v.y.data(), v.S.data(), v.sc) != SCGAL_OK) return;
+        std::lock_guard<std::mutex> lk(mu);
+        saved_bytes += v.bytes();
+        saved[s.req.id] = std::move(v);
+        saved_order.push_back(s.req.id);
+        while (saved_bytes > SAVED_CAP && !saved_order.empty()) {
+            auto it = saved.find(saved_order.front());
+            if (it != saved.end()) {
+                saved_bytes -= it->second.bytes();
+                saved.erase(it);
+            }
+            saved_order.pop_front();
+        }
+    }
+
+    // A warm start from a kept iterate (same n, R and precision): z, y, S, p and
+    // tau as kept, t at a quarter of the kept t.  Returns the starting t (1: cold).
+    long long warm_start(Slot& s) {
+        const uint64_t from = (uint64_t)s.req.prm.warm_from;
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = saved.find(from);
+        if (it == saved.end()) return 1;
+        const Saved& v = it->second;
+        if (v.n != s.req.n || v.R != s.req.prm.R || v.prec != s.req.prm.precision) return 1;
+        const long long t0 = std::max<long long>(1, (long long)v.sc[2] / 4);
+        if (t0 > s.req.prm.T_max) return 1;
+        const double sc[4] = {v.sc[0], v.sc[1], (double)t0, 0.0};
+        if (scgal_set_state(s.h, v.z.data(), v.y.data(), v.S.data(), sc) != SCGAL_OK) return 1;
+        return t0;
+    }
+
     void retire(Slot& s) {
         s.fin = false;
         publish(s, s.fin_status, s.fin_has_st ? &s.fin_st : nullptr);
@@ -181,8 +239,9 @@ struct scgal_server {
         std::memset(&r, 0, sizeof(r));
         r.status = status;
         r.n = s.req.n;
+        r.first_t = s.req.first_t;
         if (st) {
-            r.iterations = st->converged ? st->t - 1 : st->t;
+            r.iterations = (st->converged ? st->t - 1 : st->t) - (s.req.first_t - 1);
             r.relgap = st->relgap;
             r.infeas = st->infeas;
             r.objective = st->p;
@@ -198,6 +257,7 @@ struct scgal_server {
                 r.status = rc;
             }
         }
+        if (status >= 0 && s.h && s.req.kind == 0 && s.req.prm.keep_state) keep(s);
         const double t = now_ms();
         r.queue_ms = s.req.t_admit - s.req.t_submit;
         r.latency_ms = t - s.req.t_submit;
@@ -316,6 +376,7 @@ struct scgal_server {
                     finish(s, rc, nullptr);
                     continue;
                 }
+                if (s.req.kind == 0 && s.req.prm.warm_from) s.req.first_t = warm_start(s);
                 // small FP32 instances join the batched engine (else, or if its set-up
                 // fails, they run on the handle's own graphs)
                 s.batched = batch_ok && scgal::batch_eligible(s.h) && !scgal::batch_prepare(s.h, slot_desc.data()) &&

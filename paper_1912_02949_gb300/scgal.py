@@ -41,7 +41,8 @@ class scgal_params(Structure):
     _fields_ = [("R", c_int32), ("T_max", c_int32), ("tol", c_double), ("beta0", c_double), ("K", c_double),
                 ("lmo", c_int32), ("scale", c_int32), ("trace_correct", c_int32), ("precision", c_int32),
                 ("seed", c_uint64), ("instance", c_uint32), ("check_every", c_int32), ("device", c_int32),
-                ("omega", c_int32), ("kset", c_int32), ("tune", c_int32), ("spmv", c_int32), ("fft", c_int32)]
+                ("omega", c_int32), ("kset", c_int32), ("tune", c_int32), ("spmv", c_int32), ("fft", c_int32),
+                ("keep_state", c_int32), ("warm_from", c_int64)]
 
 
 class scgal_stats(Structure):
@@ -65,7 +66,7 @@ class scgal_info(Structure):
 class scgal_result(Structure):
     _fields_ = [("status", c_int32), ("n", c_int32), ("iterations", c_int64), ("relgap", c_double),
                 ("infeas", c_double), ("objective", c_double), ("best_cut", c_int64), ("lambda_max", c_double),
-                ("queue_ms", c_double), ("latency_ms", c_double)]
+                ("queue_ms", c_double), ("latency_ms", c_double), ("first_t", c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
