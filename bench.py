@@ -123,7 +123,7 @@ SERVE_DESC = ("batched serving slice: Poisson arrivals at 200 req/s, n log-unifo
               "degree U[4, 16], unit weights, R=10, solved to relative gap 1e-3 (T_max=3000), FP32 path")
 
 
-def run_serving(S, count: int, slots: int, seed: int, T_max: int = 3000, precision: int = 32):
+def run_serving(S, count: int, slots: int, seed: int, T_max: int = 3000, precision: int = 32, admission: int = 0):
     """The first `count` requests of the batched-serving workload through the
     server API (submit at the arrival times, poll every result).  Returns the
     throughput / latency summary and the raw latencies (ms)."""
@@ -136,6 +136,7 @@ def run_serving(S, count: int, slots: int, seed: int, T_max: int = 3000, precisi
         rp, col, _ = g.csr()
         graphs.append((rp, col))
     srv = S.scgal_server_create(64 << 30, slots)
+    S.scgal_server_set_admission(srv, admission)
     t0 = time.perf_counter()
     tickets = []
     for r, (rp, col) in zip(reqs, graphs):
@@ -159,6 +160,7 @@ def run_serving(S, count: int, slots: int, seed: int, T_max: int = 3000, precisi
            "rounds": st["rounds"], "worker_ms": {"wait": st["wait_ms"], "admit": st["admit_ms"],
                                                   "retire": st["retire_ms"]},
            "device_bytes_peak": st["device_bytes_peak"], "precision": precision,
+           "admission": "shortest predicted work first" if admission else "oldest first",
            "desc": SERVE_DESC.replace("FP32 path", f"FP{precision} path")}
     return out, lat.tolist()
 
@@ -589,6 +591,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=256,
                     help="requests of the batched-serving slice (0: skip the serving leg)")
     ap.add_argument("--serve-slots", type=int, default=152)
+    ap.add_argument("--no-serve-predicted", action="store_true",
+                    help="skip the serving slice admitted by least predicted work")
     ap.add_argument("--serve-twin", type=int, default=64,
                     help="requests of the FP32-vs-FP64 serving comparison (0: skip)")
     ap.add_argument("--no-phase", action="store_true", help="skip the phase-retrieval leg")
@@ -804,6 +808,12 @@ def main():
             tw64, _ = run_serving(S, args.serve_twin, args.serve_slots, seed=replica_seed(rank), precision=64)
             serving["twin"] = {"requests": args.serve_twin, "fp32": tw32, "fp64": tw64,
                                "fp32_over_fp64_solves_per_s": tw32["solves_per_s"] / tw64["solves_per_s"]}
+        if not args.no_serve_predicted:
+            # the same slice admitted by least predicted work (the model learns from the
+            # requests this server has finished), against the default oldest-first order
+            pa, _ = run_serving(S, args.serve_requests, args.serve_slots, seed=replica_seed(rank), admission=1)
+            serving["predicted_admission"] = {k: pa[k] for k in ("admission", "solves_per_s", "p50_ms", "p99_ms",
+                                                                  "queue_p50_ms", "converged", "wall_s")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "er2p20":

@@ -357,6 +357,9 @@ typedef struct {
     double   queue_ms;      /* submit -> admission */
     double   latency_ms;    /* submit -> result ready */
     int64_t  first_t;       /* the iteration the solve started at: 1, or the warm start's t */
+    double   predicted_iterations;   /* the server's estimate when the request was queued: the
+                                        mean (geometric) of the iterations finished requests of
+                                        the same size bucket took (see scgal_server_set_admission) */
 } scgal_result;
 
 typedef struct {
@@ -372,6 +375,18 @@ typedef struct {
 /* hbm_budget: bytes the server may hold on the device (admission control);
  * max_slots: solves resident at once (1..256). */
 int scgal_server_create(size_t hbm_budget, int32_t max_slots, scgal_srv_t* out);
+
+/* Admission order of the queued requests (serving policy; the paper serves no
+ * queue).  SCGAL_ADMIT_FIFO (default): oldest first.  SCGAL_ADMIT_SHORTEST_PREDICTED:
+ * when a slot frees, the request with the least predicted work among the first
+ * 256 queued -- predicted iterations x stored entries -- where the predicted
+ * iterations are the geometric mean of what the finished MaxCut requests of
+ * the same size bucket (floor(log2 n), average degree rounded to 4) took to
+ * reach their tolerance (or T_max), falling back to the nearest bucket, to all
+ * of them, or to T_max / 2; a request queued for more than a second goes first
+ * (oldest first), so none waits indefinitely.  SCGAL_EINVAL for another value. */
+enum { SCGAL_ADMIT_FIFO = 0, SCGAL_ADMIT_SHORTEST_PREDICTED = 1 };
+int scgal_server_set_admission(scgal_srv_t s, int32_t policy);
 
 /* Queue a MaxCut solve (arguments as scgal_create_maxcut; the data is copied
  * before return).  params->tol and params->T_max bound the solve.  Non-blocking;

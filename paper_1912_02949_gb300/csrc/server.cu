@@ -1,7 +1,9 @@
 // Serving loop of libscgal: continuous batching of MaxCut SDP solves.
 //
 // A worker thread owns up to max_slots resident solves.  Each round it
-//   1. admits queued requests, oldest first, while a slot is free and the
+//   1. admits queued requests (oldest first, or -- SCGAL_ADMIT_SHORTEST_PREDICTED --
+//      least predicted work first, from the iterations the finished requests of
+//      the same size took) while a slot is free and the
 //      request's estimated device footprint fits the remaining budget (the
 //      solve's z, y, sketch and Lanczos basis then stay on the device until it
 //      finishes);
@@ -52,6 +54,45 @@ struct Request {
     double t_submit = 0, t_admit = 0;
     size_t footprint = 0;
     long long first_t = 1;              // 1, or the iteration a warm start resumed at
+    double predicted_iters = 0;         // the work model's estimate when the request was queued
+};
+
+// Iterations to finish (gap and infeasibility at tol, else T_max) of the
+// requests served so far, by size bucket: floor(log2 n) and the average degree
+// rounded to a multiple of four.  Each bucket keeps the mean of log iterations;
+// a new request is predicted from its bucket, else the nearest bucket of the
+// same degree, else all buckets, else T_max / 2.
+struct WorkModel {
+    std::map<std::pair<int, int>, std::pair<double, long long>> b;   // (sum of log T, count)
+    static std::pair<int, int> key(int n, long long nnz) {
+        int lg = 0;
+        while ((2LL << lg) <= n) ++lg;
+        const int deg = (int)((nnz / std::max(1, n) + 2) / 4) * 4;
+        return {lg, deg};
+    }
+    void add(int n, long long nnz, long long iters) {
+        auto& e = b[key(n, nnz)];
+        e.first += std::log((double)std::max<long long>(1, iters));
+        ++e.second;
+    }
+    double predict(int n, long long nnz, int T_max) const {
+        const auto k = key(n, nnz);
+        auto it = b.find(k);
+        if (it != b.end()) return std::exp(it->second.first / it->second.second);
+        double best = -1, dist = 1e9, all = 0;
+        long long cnt = 0;
+        for (const auto& e : b) {
+            all += e.second.first;
+            cnt += e.second.second;
+            if (e.first.second == k.second && std::abs(e.first.first - k.first) < dist) {
+                dist = std::abs(e.first.first - k.first);
+                best = std::exp(e.second.first / e.second.second);
+            }
+        }
+        if (best > 0) return best;
+        if (cnt) return std::exp(all / cnt);
+        return 0.5 * T_max;
+    }
 };
 
 // Final iterate of a finished request submitted with keep_state (host copies).
@@ -135,6 +176,30 @@ struct scgal_server {
     std::deque<uint64_t> saved_order;
     size_t saved_bytes = 0;
     static constexpr size_t SAVED_CAP = size_t(1) << 30;
+    // admission: FIFO, or shortest predicted work first with aging
+    int admission = SCGAL_ADMIT_FIFO;
+    WorkModel model;
+    static constexpr double AGE_MS = 1000.0;   // older queued requests go first, oldest first
+    static constexpr size_t ADMIT_WINDOW = 256;
+
+    // Index in the queue of the next request to admit (guarded by mu).
+    size_t pick_next() const {
+        if (admission == SCGAL_ADMIT_FIFO || queue.size() < 2) return 0;
+        const double now = now_ms();
+        if (now - queue.front().t_submit > AGE_MS) return 0;   // aged: the oldest first
+        size_t best = 0;
+        double bw = 0;
+        const size_t lim = std::min(queue.size(), ADMIT_WINDOW);
+        for (size_t k = 0; k < lim; ++k) {
+            const Request& r = queue[k];
+            const double work = r.predicted_iters * (double)std::max<long long>(r.nnz, r.n);
+            if (k == 0 || work < bw) {
+                best = k;
+                bw = work;
+            }
+        }
+        return best;
+    }
     // batched engine state (device arrays owned by the worker thread)
     cudaStream_t bstream = nullptr;
     char* d_slots = nullptr;
@@ -240,6 +305,7 @@ struct scgal_server {
         r.status = status;
         r.n = s.req.n;
         r.first_t = s.req.first_t;
+        r.predicted_iterations = s.req.predicted_iters;
         if (st) {
             r.iterations = (st->converged ? st->t - 1 : st->t) - (s.req.first_t - 1);
             r.relgap = st->relgap;
@@ -264,6 +330,7 @@ struct scgal_server {
         if (s.h) scgal_destroy(s.h);
         s.h = nullptr;
         std::lock_guard<std::mutex> lk(mu);
+        if (st && s.req.kind == 0 && s.req.first_t == 1 && status >= 0) model.add(s.req.n, s.req.nnz, r.iterations);
         done[s.req.id] = r;
         in_use -= s.req.footprint;
         s.active = false;
@@ -298,7 +365,8 @@ struct scgal_server {
                 }
                 for (int i = 0; i < max_slots && !queue.empty(); ++i) {
                     if (slots[i].active) continue;
-                    Request& r = queue.front();
+                    const size_t qi = pick_next();
+                    Request& r = queue[qi];
                     if (in_use + r.footprint > budget) {
                         if (active == 0 && r.footprint > budget) {   // can never fit: reject
                             scgal_result res;
@@ -307,7 +375,7 @@ struct scgal_server {
                             res.n = r.n;
                             done[r.id] = res;
                             ++rejected;
-                            queue.pop_front();
+                            queue.erase(queue.begin() + (long)qi);
                             cv_done.notify_all();
                             --i;
                             continue;
@@ -315,7 +383,7 @@ struct scgal_server {
                         break;
                     }
                     slots[i].req = std::move(r);
-                    queue.pop_front();
+                    queue.erase(queue.begin() + (long)qi);
                     slots[i].active = true;
                     slots[i].h = nullptr;
                     in_use += slots[i].req.footprint;
@@ -442,6 +510,13 @@ int scgal_server_create(size_t hbm_budget, int32_t max_slots, scgal_srv_t* out) 
     return SCGAL_OK;
 }
 
+int scgal_server_set_admission(scgal_srv_t s, int32_t policy) {
+    if (!s || (policy != SCGAL_ADMIT_FIFO && policy != SCGAL_ADMIT_SHORTEST_PREDICTED)) return SCGAL_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->admission = policy;
+    return SCGAL_OK;
+}
+
 int scgal_submit(scgal_srv_t s, const int32_t* row_ptr, const int32_t* col, const double* w, int32_t n, int64_t nnz,
                  const scgal_params* params, uint64_t* ticket) {
     if (!s || !row_ptr || (nnz > 0 && !col) || !params || !ticket || n < 2 || nnz < 0) return SCGAL_EINVAL;
@@ -471,6 +546,7 @@ int scgal_submit(scgal_srv_t s, const int32_t* row_ptr, const int32_t* col, cons
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stopping) return SCGAL_ESTATE;
     if (s->queue.size() >= scgal_server::QUEUE_MAX) return SCGAL_EBUSY;
+    r.predicted_iters = s->model.predict(n, nnz, params->T_max);
     r.id = s->next_id++;
     *ticket = r.id;
     ++s->submitted;

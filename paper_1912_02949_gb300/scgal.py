@@ -29,6 +29,7 @@ SCGAL_OMEGA_STORED, SCGAL_OMEGA_REGEN = 0, 1
 SCGAL_K_EQ, SCGAL_K_LEQ = 0, 1
 SCGAL_SPMV_AUTO, SCGAL_SPMV_GATHER, SCGAL_SPMV_TILED = 0, 1, 2
 SCGAL_FFT_AUTO, SCGAL_FFT_PASSES, SCGAL_FFT_CLUSTER = 0, 1, 2
+SCGAL_ADMIT_FIFO, SCGAL_ADMIT_SHORTEST_PREDICTED = 0, 1
 
 
 class ScgalError(RuntimeError):
@@ -66,7 +67,8 @@ class scgal_info(Structure):
 class scgal_result(Structure):
     _fields_ = [("status", c_int32), ("n", c_int32), ("iterations", c_int64), ("relgap", c_double),
                 ("infeas", c_double), ("objective", c_double), ("best_cut", c_int64), ("lambda_max", c_double),
-                ("queue_ms", c_double), ("latency_ms", c_double), ("first_t", c_int64)]
+                ("queue_ms", c_double), ("latency_ms", c_double), ("first_t", c_int64),
+                ("predicted_iterations", c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -105,6 +107,7 @@ _PROTOS = {
     "scgal_destroy": (c_int, [c_void_p]),
     "scgal_strerror": (c_char_p, [c_int]),
     "scgal_server_create": (c_int, [c_size_t, c_int32, POINTER(c_void_p)]),
+    "scgal_server_set_admission": (c_int, [c_void_p, c_int32]),
     "scgal_submit": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int64, POINTER(scgal_params),
                              POINTER(c_uint64)]),
     "scgal_submit_phase": (c_int, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, POINTER(scgal_params),
@@ -362,6 +365,10 @@ def scgal_server_create(hbm_budget: int, max_slots: int) -> Server:
     s = c_void_p()
     _check(load().scgal_server_create(int(hbm_budget), int(max_slots), ctypes.byref(s)), "scgal_server_create")
     return Server(s)
+
+
+def scgal_server_set_admission(s: Server, policy: int) -> None:
+    _check(load().scgal_server_set_admission(s.raw, int(policy)), "scgal_server_set_admission")
 
 
 def scgal_submit(s: Server, row_ptr, col, w, n: int, nnz: int, params: scgal_params) -> int:
