@@ -287,8 +287,9 @@ int scgal_get_info(scgal_t h, scgal_info* out);
  * on the handle's stream between two CUDA events and report the mean duration
  * of one launch in milliseconds.  kernel: 0 the first Lanczos D-matvec step
  * (MaxCut: the CSR kernel with the omega reduction, or the two tiled passes;
- * phase retrieval: the FFT kernel(s)), 1 the three-term update as a launch of
- * its own, 2 the Ritz vector, 3 the tridiagonal eigensolver, 4 one Lanczos
+ * coded diffraction: the FFT kernel(s); ptychography: the window kernel, whose
+ * per-pixel window sum the update takes), 1 the three-term update as a launch
+ * of its own, 2 the Ritz vector, 3 the tridiagonal eigensolver, 4 one Lanczos
  * step as the solver runs it (D-matvec and three-term update in sequence):
  * the mean over the q steps of about reps / q whole Lanczos runs.  Works on the iteration t the handle
  * is about to run, with private scalars: the solver state is unchanged (only

@@ -169,7 +169,8 @@ int setup_state(scgal_ctx* h) {
     ALLOC(h, p.sv, sizeof(double) * (h->qmax + 2));
     ALLOC(h, p.coef, sizeof(double) * (h->qmax + 2));
     ALLOC(h, p.hist, sizeof(scgal_stats) * (size_t)hist_cap);
-    p.nupd = update_grid<V>(n);   // blocks of every Lanczos update launch (one partial each)
+    // blocks of every Lanczos update launch (one partial each)
+    p.nupd = (h->c.kind == KIND_PTYCHO) ? fp_update_grid(n) : update_grid<V>(n);
     p.upcap = std::max(gmax, p.nupd);
     ALLOC(h, p.upart, sizeof(double) * 2 * (size_t)p.upcap);   // two buffers (step parity)
     {

@@ -242,33 +242,87 @@ __device__ __forceinline__ double strided_sum_cg(const double* __restrict__ x, i
 }
 
 // --------------------------------------------------------------------------
-// Deterministic grid reduction of NV doubles (blockDim.x == BS, a multiple of
-// 32; 1-D or 2-D grids, blocks numbered blockIdx.y * gridDim.x + blockIdx.x).
-// Returns true in exactly one block (the last to arrive); there tot[0..NV)
-// (shared memory) holds the grid totals for every thread after the call.
-template <int NV, typename WT = double, int BS = SCGAL_BS>
-__device__ __forceinline__ bool grid_reduce(WT (&v)[NV], double* __restrict__ partials,
-                                            unsigned* __restrict__ ticket, double* tot) {
-    // WT: type of the warp-level sums (float on the FP32 path: FP64 arithmetic is
-    // scarce on GB300); warp, block and grid totals are then added in FP64.
-    __shared__ double red[BS / 32][NV];
+// Float-float sums.  FP64 instructions are scarce on GB300 (a warp-wide FP64
+// add occupies an SM's FP64 units for about as long as sixteen FP32 ones), so
+// the FP32 path carries its block sums as unevaluated pairs s + c of floats:
+// a two-sum of the leading parts, their rounding error folded into the
+// trailing parts, then renormalised (Dekker's double-length addition without
+// the final refinement).  About 44 significant bits, FP32 instructions only.
+struct FF {
+    float s, c;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float t = __fadd_rn(a.s, b.s);
+    const float bb = __fsub_rn(t, a.s);
+    const float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bb)), __fsub_rn(b.s, bb));
+    const float c = __fadd_rn(__fadd_rn(a.c, b.c), e);
+    const float r = __fadd_rn(t, c);
+    return FF{r, __fsub_rn(c, __fsub_rn(r, t))};
+}
+
+// This block's total (blockDim.x == BS) of every thread's value, in a fixed
+// order, returned to thread 0 (0 elsewhere).  An FP32 CompSum is reduced as a
+// float-float pair and turned into a double once; doubles are added as such.
+// One call per kernel (its shared buffer is reused by the next call).
+template <int BS>
+__device__ __forceinline__ double block_total(const CompSum<float>& a) {
+    __shared__ FF red[BS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    FF v{a.s, a.c};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const FF w{__shfl_down_sync(0xffffffffu, v.s, o), __shfl_down_sync(0xffffffffu, v.c, o)};
+        v = ff_add(v, w);
+    }
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double out = 0.0;
+    if (threadIdx.x == 0) {
+        FF t = red[0];
+#pragma unroll
+        for (int w = 1; w < BS / 32; ++w) t = ff_add(t, red[w]);
+        out = (double)t.s + (double)t.c;
+    }
+    return out;
+}
+template <int BS>
+__device__ __forceinline__ double block_total(double v) {
+    __shared__ double red[BS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double out = 0.0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 0; w < BS / 32; ++w) out += red[w];
+    }
+    return out;
+}
+template <int BS>
+__device__ __forceinline__ double block_total(const CompSum<double>& a) {
+    return block_total<BS>(a.total());
+}
+
+// --------------------------------------------------------------------------
+// The grid part of a deterministic reduction of NV doubles (blockDim.x == BS,
+// a multiple of 32; 1-D or 2-D grids, blocks numbered blockIdx.y * gridDim.x +
+// blockIdx.x): thread k < NV holds this block's total k in `mine`.  Returns
+// true in exactly one block (the last to arrive); there tot[0..NV) (shared
+// memory) holds the grid totals for every thread after the call.  Partials
+// are added in block order, so the result does not depend on scheduling.
+// ticket[0] must be 0 on entry; the last block resets it.
+template <int NV, int BS>
+__device__ __forceinline__ bool grid_tail(double mine, double* __restrict__ partials, unsigned* __restrict__ ticket,
+                                          double* tot) {
+    __shared__ double red[BS / 32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned nblk = gridDim.x * gridDim.y;
     const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        WT x = v[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[wid][k] = (double)x;
-    }
-    __syncthreads();
     if (threadIdx.x < NV) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < BS / 32; ++w) s += red[w][threadIdx.x];
-        partials[(size_t)threadIdx.x * nblk + bid] = s;
+        partials[(size_t)threadIdx.x * nblk + bid] = mine;
         __threadfence();   // this block's partials are visible before its ticket
     }
     __syncthreads();
@@ -285,12 +339,12 @@ __device__ __forceinline__ bool grid_reduce(WT (&v)[NV], double* __restrict__ pa
         s = strided_sum_cg<BS>(partials + (size_t)k * nblk, (int)nblk, s);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) red[wid][0] = s;
+        if (lane == 0) red[wid] = s;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
 #pragma unroll
-            for (int w = 0; w < BS / 32; ++w) t += red[w][0];
+            for (int w = 0; w < BS / 32; ++w) t += red[w];
             tot[k] = t;
         }
         __syncthreads();
@@ -300,21 +354,27 @@ __device__ __forceinline__ bool grid_reduce(WT (&v)[NV], double* __restrict__ pa
     return true;
 }
 
-// Block-level sum of one value into `out` (thread 0 writes), fixed order.
-template <typename WT>
-__device__ __forceinline__ void block_sum_to(WT v, double* out) {
-    __shared__ double red[SCGAL_BS / 32];
+// Deterministic grid reduction of NV values per thread: warp sums in WT (float
+// on the FP32 path), block and grid totals in FP64 (grid_tail).
+template <int NV, typename WT = double, int BS = SCGAL_BS>
+__device__ __forceinline__ bool grid_reduce(WT (&v)[NV], double* __restrict__ partials,
+                                            unsigned* __restrict__ ticket, double* tot) {
+    __shared__ double red[BS / 32][NV];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wid] = (double)v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
+    for (int k = 0; k < NV; ++k) {
+        WT x = v[k];
 #pragma unroll
-        for (int w = 0; w < SCGAL_BS / 32; ++w) s += red[w];
-        *out = s;
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[wid][k] = (double)x;
     }
+    __syncthreads();
+    double mine = 0.0;
+    if (threadIdx.x < NV) {
+#pragma unroll
+        for (int w = 0; w < BS / 32; ++w) mine += red[w][threadIdx.x];
+    }
+    return grid_tail<NV, BS>(mine, partials, ticket, tot);
 }
 
 // Block-wide fixed-order sum of x[0..m) (every thread receives the total;

@@ -177,22 +177,15 @@ __device__ __forceinline__ void finish_lanczos_scalars(const KP<V>& p, int i, do
 }
 
 // A D-matvec step's share of <W_i, D W_i>: the block's threads' values added in
-// a fixed order, written to partials[block] (flattened 2-D block index); block 0
-// also records the number of partials in ticket[2].  No grid-wide wait: the
-// kernel that follows (the update, or the tridiagonal solve after the last
-// step) adds the partials up (step_sums) and finishes the step.
-template <int BS>
-__device__ __forceinline__ void write_step_partial(double* partials, unsigned* ticket, double v) {
-    __shared__ double red[BS / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
+// a fixed order (block_total), written to partials[block] (flattened 2-D block
+// index); block 0 also records the number of partials in ticket[2].  No
+// grid-wide wait: the kernel that follows (the update, or the tridiagonal solve
+// after the last step) adds the partials up (step_coeffs / step_sums) and
+// finishes the step.
+template <int BS, typename A>
+__device__ __forceinline__ void write_step_partial(double* partials, unsigned* ticket, const A& v) {
+    const double t = block_total<BS>(v);
     if (threadIdx.x == 0) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < BS / 32; ++w) t += red[w];
         const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
         partials[bid] = t;
         if (bid == 0) ticket[2] = gridDim.x * gridDim.y;
@@ -219,53 +212,95 @@ __device__ __forceinline__ void finish_lanczos_step(const KP<V>& p, int i, doubl
     if (threadIdx.x == 0) finish_lanczos_scalars(p, i, dot, rr);
 }
 
-// A step kernel's <W_i, D W_i>: with p.fin_upd its block partial (the update
-// ends the step), else the grid reduction whose last block ends the step.
-template <typename V, int BS>
-__device__ __forceinline__ void step_dot(const KP<V>& p, int i, double v) {
+// A step kernel's <W_i, D W_i> (a CompSum or a double per thread): with
+// p.fin_upd its block partial (the update ends the step), else the grid
+// reduction whose last block ends the step.
+template <typename V, int BS, typename A>
+__device__ __forceinline__ void step_dot(const KP<V>& p, int i, const A& v) {
     if (p.fin_upd) {
         write_step_partial<BS>(p.partials, p.ticket, v);
     } else {
-        double a[1] = {v};
+        const double bt = block_total<BS>(v);
         __shared__ double tot[1];
-        if (grid_reduce<1, double, BS>(a, p.partials, p.ticket, tot)) finish_lanczos_step<V, BS>(p, i, tot[0]);
+        if (grid_tail<1, BS>(bt, p.partials, p.ticket, tot)) finish_lanczos_step<V, BS>(p, i, tot[0]);
     }
 }
 
-// Every thread of a block of BS threads receives dot = sum of the step's
-// partials and rr = ||W_i||^2 (the previous update's partials), each added in
-// the same fixed order in every block.
-template <typename V, int BS>
-__device__ __forceinline__ void step_sums(const KP<V>& p, int i, double& dot, double& rr) {
-    __shared__ double r1[BS / 32], r2[BS / 32];
-    __shared__ double res[2];
+// The sums that end step i, taken by the 32 threads of warp 0 (valid in its
+// lane 0): dot = <W_i, D W_i> from the step's partials, rr = ||W_i||^2 from the
+// previous update's; the same fixed order in every block.  One warp keeps the
+// FP64 additions few (they are scarce on GB300).
+template <typename V>
+__device__ __forceinline__ void step_sums_warp(const KP<V>& p, int i, double& dot, double& rr) {
     const int nd = (int)__ldcg(p.ticket + 2);
-    double s1 = strided_sum_cg<BS>(p.partials, nd);
-    double s2 = (i > 0) ? strided_sum_cg<BS>(upart_of(p, i), p.nupd) : 0.0;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double s1 = strided_sum_cg<32>(p.partials, nd);
+    double s2 = (i > 0) ? strided_sum_cg<32>(upart_of(p, i), p.nupd) : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_down_sync(0xffffffffu, s1, o);
         s2 += __shfl_down_sync(0xffffffffu, s2, o);
     }
-    if (lane == 0) {
-        r1[wid] = s1;
-        r2[wid] = s2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-#pragma unroll
-        for (int w = 0; w < BS / 32; ++w) {
-            a += r1[w];
-            b += r2[w];
+    // ptychography: the window kernel's partials hold sum_j w_j |W*_m Phi_j W_i|^2;
+    // D = sC I + (the window terms), so <W_i, D W_i> adds sC ||W_i||^2
+    if (p.c.kind == KIND_PTYCHO) s1 += p.c.sC * ((i > 0) ? s2 : 1.0 / (p.sv[0] * p.sv[0]));
+    dot = s1;
+    rr = s2;
+}
+
+// Every thread of a block of BS threads receives the sums of step_sums_warp.
+template <typename V, int BS>
+__device__ __forceinline__ void step_sums(const KP<V>& p, int i, double& dot, double& rr) {
+    __shared__ double res[2];
+    if (threadIdx.x < 32) {
+        double d, r;
+        step_sums_warp(p, i, d, r);
+        if (threadIdx.x == 0) {
+            res[0] = d;
+            res[1] = r;
         }
-        res[0] = a;
-        res[1] = b;
     }
     __syncthreads();
     dot = res[0];
     rr = res[1];
+}
+
+// The coefficients of the update of step i, W_{i+1} = a Y + b W_i + c W_{i-1}
+// (a = s_i, b = -omega_i s_i, c = -rho_{i-1} s_{i-1}), for every thread.  With
+// p.fin_upd the step ends here (step_sums_warp; block 0 records it), else its
+// recorded scalars are read.  One thread takes the FP64 square root and
+// divisions and hands the block the coefficients through shared memory.
+template <typename V, int BS>
+__device__ __forceinline__ void step_coeffs(const KP<V>& p, int i, typename VT<V>::R& a, typename VT<V>::R& b,
+                                            typename VT<V>::R& c) {
+    typedef typename VT<V>::R Rt;
+    __shared__ Rt co[3];
+    if (threadIdx.x < 32) {
+        double si = 0.0, om = 0.0, rho = 0.0;
+        if (p.fin_upd) {
+            double dot, rr;
+            step_sums_warp(p, i, dot, rr);
+            if (threadIdx.x == 0) {
+                if (blockIdx.x == 0) finish_lanczos_scalars(p, i, dot, rr);
+                const StepScalars ss = step_scalars(p, i, dot, rr);
+                si = ss.s;
+                om = ss.om;
+                rho = ss.rho;
+            }
+        } else if (threadIdx.x == 0) {
+            si = p.sv[i];
+            om = p.om[i];
+            rho = (i > 0) ? p.rh[i - 1] : 0.0;
+        }
+        if (threadIdx.x == 0) {
+            co[0] = (Rt)si;
+            co[1] = (Rt)(-om * si);
+            co[2] = (i > 0) ? (Rt)(-rho * p.sv[i - 1]) : (Rt)0;
+        }
+    }
+    __syncthreads();
+    a = co[0];
+    b = co[1];
+    c = co[2];
 }
 
 }  // namespace scgal
@@ -401,6 +436,8 @@ template <typename V> void launch_dvec_from_w(const KP<V>& p, int grid, const do
 
 // Phase retrieval
 template <typename V> void launch_phase_step(const KP<V>& p, int i, cudaStream_t s);
+template <typename V> void launch_fp_lanczos_update(const KP<V>& p, int i, cudaStream_t s);
+int fp_update_grid(long long n);
 template <typename V> void launch_phase_update(const KP<V>& p, int grid, cudaStream_t s);
 template <typename V> void launch_apply_D_phase(const KP<V>& p, const V* x, V* out, const typename VT<V>::R* w, cudaStream_t s);
 template <typename V> void launch_wvec_from_w(const KP<V>& p, int grid, const double* w, cudaStream_t s);

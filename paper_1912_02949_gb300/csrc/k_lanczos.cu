@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_dual_start(KP<V> p, int do_dual) {
 // ---------------------------------------------------------------------------
 // With p.fin_upd the update first ends step i: every block adds up the step's
 // <W_i, D W_i> partials and the previous update's ||W_i||^2 partials in the
-// same fixed order (step_sums), so all blocks derive the same s_i, omega_i,
+// same fixed order (step_coeffs), so all blocks derive the same s_i, omega_i,
 // rho_{i-1}, and block 0 records them (finish_lanczos_scalars); cheap for the
 // phase-retrieval steps' few partials, while the MaxCut steps' many partials
 // read by every block of a large update grid would crowd the L2 lines holding
@@ -122,23 +122,8 @@ __global__ void __launch_bounds__(SCGAL_BS, 4) k_lanczos_update(KP<V> p, int i) 
     constexpr int UN = 2;              // 16-byte groups per thread in flight
     struct alignas(16) RV { Rt v[W]; };
     pdl_wait();
-    double si, om, rho;
-    if (p.fin_upd) {   // end step i here (see above); else its last block did
-        double dot, rr;
-        step_sums<V, SCGAL_BS>(p, i, dot, rr);
-        if (blockIdx.x == 0 && threadIdx.x == 0) finish_lanczos_scalars(p, i, dot, rr);
-        const StepScalars ss = step_scalars(p, i, dot, rr);
-        si = ss.s;
-        om = ss.om;
-        rho = ss.rho;
-    } else {
-        si = p.sv[i];
-        om = p.om[i];
-        rho = (i > 0) ? p.rh[i - 1] : 0.0;
-    }
-    const Rt a = (Rt)si;
-    const Rt b = (Rt)(-om * si);
-    const Rt c = (i > 0) ? (Rt)(-rho * p.sv[i - 1]) : (Rt)0;
+    Rt a, b, c;   // with p.fin_upd step i ends here (see above); else its last block ended it
+    step_coeffs<V, SCGAL_BS>(p, i, a, b, c);
     constexpr int CF = VT<V>::cplx ? 2 : 1;
     const long long m = (long long)p.c.n * CF;        // reals per vector
     const long long ldr = p.ldb * CF;                  // reals between basis rows (multiple of 64)
@@ -187,7 +172,8 @@ __global__ void __launch_bounds__(SCGAL_BS, 4) k_lanczos_update(KP<V> p, int i) 
         Wn[k] = w;
         acc.add(w, w);
     }
-    block_sum_to<double>(acc.total(), upart_of(p, i + 1) + blockIdx.x);
+    const double nb = block_total<SCGAL_BS>(acc);
+    if (threadIdx.x == 0) upart_of(p, i + 1)[blockIdx.x] = nb;
 }
 
 // With p.fin_upd, ends the run's last step (q - 1, no update follows it); then
@@ -442,6 +428,12 @@ template <typename V> int update_grid(long long n) {
 template <typename V> void launch_lanczos_update(const KP<V>& p, int grid, int i, cudaStream_t s) {
     // the grid must be the one p.nupd was sized for: the next step reads nupd partials
     (void)grid;
+    if constexpr (VT<V>::cplx) {
+        if (p.c.kind == KIND_PTYCHO) {   // forms D W_i itself from the window values
+            launch_fp_lanczos_update<V>(p, i, s);
+            return;
+        }
+    }
     launch_pdl(k_lanczos_update<V>, p.nupd, SCGAL_BS, 0, s, p, i);
 }
 template <typename V> void launch_tridiag(const KP<V>& p, int q, cudaStream_t s) {

@@ -877,7 +877,7 @@ __global__ void __launch_bounds__(NT, 1) k_phc(KP<V> p, const V* __restrict__ x,
                 if (gi < ng2 - 1) __syncthreads();
             }
         }
-        if constexpr (DOT != 0) step_dot<V, NT>(p, i, acc.total());
+        if constexpr (DOT != 0) step_dot<V, NT>(p, i, acc);
     } else {
         __syncthreads();
         DevScalars* sc = p.sc;
@@ -955,8 +955,10 @@ static void forward_and_weight(const KP<V>& p, const V* x, const typename VT<V>:
 //   D x = sC x + sum_j Phi_j^* W_m (w_j .* W*_m Phi_j x)      (w already holds sA)
 // One block per window runs both 2-D transforms in shared memory (two
 // M x (M + 1) tiles: the padded row stride keeps the column passes free of
-// bank conflicts); k_fp_gather then sums, for every pixel, the windows that
-// cover it in a fixed order (no atomics: results do not depend on scheduling).
+// bank conflicts); the windows covering each pixel are then summed in a fixed
+// order (no atomics: results do not depend on scheduling), by k_fp_gather for
+// a D x on its own and inside the Lanczos update (k_fp_lanczos_update) for
+// the steps of Alg. 4.1.
 template <typename V> size_t fp_smem(const KP<V>& p) {
     return sizeof(V) * (2 * (size_t)p.fpM * (p.fpM + 1) + (size_t)(p.fpM / 2 + 1));
 }
@@ -998,7 +1000,9 @@ __device__ void fp_window_inverse(const KP<V>& p, const V* __restrict__ x, int j
 }
 
 // fftbuf[j m + l] = (Phi_j^* W_m (w_j .* W*_m Phi_j x)) restricted to window j, l = r M + c.
-template <typename V>
+// DOT: also the window's share of the Lanczos step's <x, D x>,
+// sum_l w_jl |(W*_m Phi_j x)_l|^2, as block partial j (write_step_partial).
+template <typename V, int DOT>
 __global__ void __launch_bounds__(SCGAL_BS) k_fp_apply(KP<V> p, const V* __restrict__ x,
                                                        const typename VT<V>::R* __restrict__ w) {
     typedef typename VT<V>::R Rt;
@@ -1011,6 +1015,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_apply(KP<V> p, const V* __restr
     const int j = blockIdx.x;
     fp_window_inverse<V>(p, x, j, a, tws);
     const Rt* __restrict__ wj = w + (size_t)j * m;
+    CompSum<Rt> dacc;
     constexpr int UL = 8;
     for (int base = threadIdx.x; base < m; base += blockDim.x * UL) {
         Rt wv[UL];
@@ -1024,9 +1029,14 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_apply(KP<V> p, const V* __restr
             const int idx = base + u * blockDim.x;
             if (idx < m) {
                 const int r = idx >> lg, c = idx & (M - 1);
-                V v = a[r * LD + c];
-                v.x *= wv[u];
-                v.y *= wv[u];
+                const V uv = a[r * LD + c];
+                V v;
+                v.x = uv.x * wv[u];
+                v.y = uv.y * wv[u];
+                if constexpr (DOT) {
+                    dacc.add(v.x, uv.x);
+                    dacc.add(v.y, uv.y);
+                }
                 b[brev(r, lg) * LD + brev(c, lg)] = v;
             }
         }
@@ -1039,6 +1049,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_apply(KP<V> p, const V* __restr
         const int r = idx >> lg, c = idx & (M - 1);
         out[idx] = CX<V>::cmul(p.masks[idx], b[r * LD + c]);   // conj(pupil) * .
     }
+    if constexpr (DOT) write_step_partial<SCGAL_BS>(p.partials, p.ticket, dacc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1052,8 +1063,9 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_apply(KP<V> p, const V* __restr
 // the tile's row stride M + 1 keeps both free of bank conflicts.  Each pass
 // is a group of three radix-2 stages in registers (two groups per length-64
 // transform); the last column group of the first transform, the weight and
-// the first column group of the second run as one pass.
-template <typename V>
+// the first column group of the second run as one pass; DOT as in k_fp_apply
+// (the squares are taken in that pass, where u = W*_m Phi_j x is complete).
+template <typename V, int DOT>
 __global__ void __launch_bounds__(SCGAL_BS) k_fp_apply64(KP<V> p, const V* __restrict__ x,
                                                          const typename VT<V>::R* __restrict__ w) {
     typedef typename VT<V>::R Rt;
@@ -1121,6 +1133,7 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_apply64(KP<V> p, const V* __res
     // natural frequency (brev(row position), brev(column position)), then the
     // forward DFT's first DIT group on the same slots
     const Rt* __restrict__ wj = w + (size_t)j * m;
+    CompSum<Rt> dacc;
     for (int it = threadIdx.x; it < ITEMS; it += SCGAL_BS) {
         const int col = it & (M - 1), g = it >> LG;
         const int pos0 = g << NB;
@@ -1134,8 +1147,13 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_apply64(KP<V> p, const V* __res
         phc_small_dif<V, NB, true>(v);
 #pragma unroll
         for (int t = 0; t < P; ++t) {
-            v[t].x *= wv[t];
-            v[t].y *= wv[t];
+            const V uv = v[t];
+            v[t].x = uv.x * wv[t];
+            v[t].y = uv.y * wv[t];
+            if constexpr (DOT) {
+                dacc.add(v[t].x, uv.x);
+                dacc.add(v[t].y, uv.y);
+            }
         }
         phc_small_dit<V, NB, false>(v);
 #pragma unroll
@@ -1174,17 +1192,17 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_apply64(KP<V> p, const V* __res
     V* out = p.fftbuf + (size_t)j * m;
     for (int idx = threadIdx.x; idx < m; idx += SCGAL_BS)
         out[idx] = CX<V>::cmul(p.masks[idx], a[(idx >> LG) * LD + (idx & (M - 1))]);
+    if constexpr (DOT) write_step_partial<SCGAL_BS>(p.partials, p.ticket, dacc);
 }
 
-// out = sC x + (sum over the windows covering each pixel); DOT: also reduce
-// Re<x, D x> and finish Lanczos step i.
-template <typename V, int DOT>
-__global__ void __launch_bounds__(SCGAL_BS) k_fp_gather(KP<V> p, const V* __restrict__ x, V* __restrict__ out, int i) {
+// out = sC x + (sum over the windows covering each pixel), for a D x on its own
+// (the Lanczos steps fold this sum into k_fp_lanczos_update).
+template <typename V>
+__global__ void __launch_bounds__(SCGAL_BS) k_fp_gather(KP<V> p, const V* __restrict__ x, V* __restrict__ out) {
     typedef typename VT<V>::R Rt;
     constexpr int CF = 6;   // coverage entries held in registers (the common case: ceil(M/s) + 1 <= 6)
     const int N = p.fpN, K = p.fpK, CM = p.fpCM, lg = p.fpLogM, n = p.c.n;
     const Rt sC = (Rt)p.c.sC;
-    Rt dot = 0;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const int gr = e / N, gc = e - gr * N;
         const int2* __restrict__ cr = p.fpcov + (size_t)gr * CM;
@@ -1227,9 +1245,115 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_gather(KP<V> p, const V* __rest
         val.x = sC * xe.x + acc.x;
         val.y = sC * xe.y + acc.y;
         out[e] = val;
-        if (DOT) dot += xe.x * val.x + xe.y * val.y;
     }
-    if constexpr (DOT) step_dot<V, SCGAL_BS>(p, i, (double)dot);
+}
+
+// The windows covering coordinate g (a row or a column) of the N x N grid:
+// k = g / s - u (mod K) at offset g mod s + u s, for u = 0, 1, ... while that
+// offset is below M (the offsets form a periodic grid with K s = N).
+struct FpCover {
+    int k0, off0, cnt;
+};
+__device__ __forceinline__ FpCover fp_cover(int g, int s, int M) {
+    FpCover c;
+    c.k0 = g / s;
+    c.off0 = g - c.k0 * s;
+    c.cnt = c.off0 < M ? (M - 1 - c.off0) / s + 1 : 0;
+    return c;
+}
+
+// Lanczos update for the ptychography operator with the window sum folded in
+// (Alg. 4.1's three-term recurrence, deferred normalisation as in
+// k_lanczos_update): (D W_i)_e = sC W_i[e] + the values of the windows covering
+// pixel e (fftbuf, left by the window kernel of step i), summed over row
+// windows, then column windows, in fp_cover's order, so D W_i is never stored.
+// The step's <W_i, D W_i> is sum_j sum_l w_jl |(W*_m Phi_j W_i)_l|^2 (the
+// window kernel's partials) + sC ||W_i||^2 (step_sums_warp adds the last term).
+// The window loads of a thread's first pixels are issued before the step's
+// scalars are summed, so the two L2 round trips overlap.  Every block leaves
+// its ||W_{i+1}||^2 in upart for the end of step i+1.
+template <typename V>
+__global__ void __launch_bounds__(SCGAL_BS) k_fp_lanczos_update(KP<V> p, int i) {
+    typedef typename VT<V>::R Rt;
+    constexpr int UN = 2;   // pixels per thread in flight
+    constexpr int CU = 4;   // covering windows per dimension taken from registers
+    pdl_wait();
+    const int N = p.fpN, K = p.fpK, s = p.fpS, M = p.fpM, lg = p.fpLogM, n = p.c.n;
+    const Rt sC = (Rt)p.c.sC;
+    const V* __restrict__ Wi = p.basis + (size_t)i * p.ldb;
+    const V* __restrict__ Wm = (i > 0) ? Wi - p.ldb : Wi;
+    V* __restrict__ Wn = p.basis + (size_t)(i + 1) * p.ldb;
+    const V* __restrict__ fb = p.fftbuf;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+    const int rounds = (n + st * UN - 1) / (st * UN);   // the same in every block (step_coeffs' barrier)
+    Rt a = 0, b = 0, c = 0;
+    CompSum<Rt> nrm;
+    for (int rd = 0; rd < rounds; ++rd) {
+        V t[UN][CU * CU], xi[UN], xm[UN];
+        FpCover cr[UN], cc[UN];
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            const int e = gt + (rd * UN + u) * st;
+            cr[u].cnt = cc[u].cnt = 0;
+            if (e < n) {
+                const int gr = e / N, gc = e - gr * N;
+                cr[u] = fp_cover(gr, s, M);
+                cc[u] = fp_cover(gc, s, M);
+                xi[u] = Wi[e];
+                xm[u] = Wm[e];
+            }
+            const bool reg = cr[u].cnt <= CU && cc[u].cnt <= CU;
+#pragma unroll
+            for (int ur = 0; ur < CU; ++ur)
+#pragma unroll
+                for (int uc = 0; uc < CU; ++uc) {
+                    t[u][ur * CU + uc] = vzero<V>();
+                    if (reg && ur < cr[u].cnt && uc < cc[u].cnt) {
+                        int kr = cr[u].k0 - ur, kc = cc[u].k0 - uc;
+                        if (kr < 0) kr += K;
+                        if (kc < 0) kc += K;
+                        const int ro = cr[u].off0 + ur * s, co = cc[u].off0 + uc * s;
+                        t[u][ur * CU + uc] = fb[((size_t)(kr * K + kc) << (2 * lg)) + ((size_t)ro << lg) + co];
+                    }
+                }
+        }
+        if (rd == 0) step_coeffs<V, SCGAL_BS>(p, i, a, b, c);   // end step i
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            const int e = gt + (rd * UN + u) * st;
+            if (e >= n) continue;
+            V acc = vzero<V>();
+            if (cr[u].cnt <= CU && cc[u].cnt <= CU) {
+#pragma unroll
+                for (int q = 0; q < CU * CU; ++q) {   // absent windows hold zeros
+                    acc.x += t[u][q].x;
+                    acc.y += t[u][q].y;
+                }
+            } else {   // windows overlapping more than CU deep (s < M / CU)
+                for (int ur = 0; ur < cr[u].cnt; ++ur) {
+                    int kr = cr[u].k0 - ur;
+                    if (kr < 0) kr += K;
+                    const int ro = cr[u].off0 + ur * s;
+                    for (int uc = 0; uc < cc[u].cnt; ++uc) {
+                        int kc = cc[u].k0 - uc;
+                        if (kc < 0) kc += K;
+                        const V v = fb[((size_t)(kr * K + kc) << (2 * lg)) + ((size_t)ro << lg) + cc[u].off0 + uc * s];
+                        acc.x += v.x;
+                        acc.y += v.y;
+                    }
+                }
+            }
+            V y;
+            y.x = sC * xi[u].x + acc.x;
+            y.y = sC * xi[u].y + acc.y;
+            const V w = lin3(a, y, b, xi[u], c, xm[u]);
+            Wn[e] = w;
+            nrm.add(w.x, w.x);
+            nrm.add(w.y, w.y);
+        }
+    }
+    const double nb = block_total<SCGAL_BS>(nrm);
+    if (threadIdx.x == 0) upart_of(p, i + 1)[blockIdx.x] = nb;
 }
 
 // Primal update of the iteration (Eq. 6.2): z <- (1 - eta) z + eta A(alpha v v*)
@@ -1297,17 +1421,28 @@ __global__ void __launch_bounds__(SCGAL_BS) k_fp_update(KP<V> p) {
 // Shared memory of k_fp_apply64: one M x (M + 1) tile and the M roots.
 template <typename V> static size_t fp64_smem() { return sizeof(V) * (64 * 65 + 64); }
 
-template <typename V>
+template <typename V, int DOT>
 static void launch_fp_apply(const KP<V>& p, const V* x, const typename VT<V>::R* w, cudaStream_t s) {
-    if (p.fpM == 64) k_fp_apply64<V><<<p.c.L, SCGAL_BS, fp64_smem<V>(), s>>>(p, x, w);
-    else k_fp_apply<V><<<p.c.L, SCGAL_BS, fp_smem(p), s>>>(p, x, w);
+    if (p.fpM == 64) k_fp_apply64<V, DOT><<<p.c.L, SCGAL_BS, fp64_smem<V>(), s>>>(p, x, w);
+    else k_fp_apply<V, DOT><<<p.c.L, SCGAL_BS, fp_smem(p), s>>>(p, x, w);
+}
+
+// Blocks of k_fp_lanczos_update: one round of UN = 2 pixels per thread (one
+// ||W||^2 partial per block).
+int fp_update_grid(long long n) { return (int)std::max<long long>(1, (n + 2LL * SCGAL_BS - 1) / (2LL * SCGAL_BS)); }
+
+template <typename V> void launch_fp_lanczos_update(const KP<V>& p, int i, cudaStream_t s) {
+    launch_pdl(k_fp_lanczos_update<V>, p.nupd, SCGAL_BS, 0, s, p, i);
 }
 
 template <typename V> int prepare_fp_kernels(const KP<V>& p) {
     const int sm = (int)fp_smem(p);
-    cudaError_t e = cudaFuncSetAttribute(k_fp_apply<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaError_t e = cudaFuncSetAttribute(k_fp_apply<V, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fp_apply<V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fp_apply64<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp64_smem<V>());
+        e = cudaFuncSetAttribute(k_fp_apply64<V, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp64_smem<V>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fp_apply64<V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp64_smem<V>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fp_update<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1413,9 +1548,8 @@ template <typename V> int prepare_phase_cluster(const KP<V>& p, int L) {
 
 template <typename V> void launch_phase_step(const KP<V>& p, int i, cudaStream_t s) {
     const V* x = p.basis + (size_t)i * p.ldb;
-    if (p.c.kind == KIND_PTYCHO) {
-        launch_fp_apply<V>(p, x, p.wvec, s);
-        k_fp_gather<V, 1><<<p.fpGrid, SCGAL_BS, 0, s>>>(p, x, p.ybuf, i);
+    if (p.c.kind == KIND_PTYCHO) {   // the window sum is taken by the update (k_fp_lanczos_update)
+        launch_fp_apply<V, 1>(p, x, p.wvec, s);
         return;
     }
     // the passes skip nothing on breakdown; only their cost is wasted
@@ -1444,8 +1578,8 @@ template <typename V> void launch_phase_update(const KP<V>& p, int grid, cudaStr
 template <typename V>
 void launch_apply_D_phase(const KP<V>& p, const V* x, V* out, const typename VT<V>::R* w, cudaStream_t s) {
     if (p.c.kind == KIND_PTYCHO) {
-        launch_fp_apply<V>(p, x, w, s);
-        k_fp_gather<V, 0><<<p.fpGrid, SCGAL_BS, 0, s>>>(p, x, out, 0);
+        launch_fp_apply<V, 0>(p, x, w, s);
+        k_fp_gather<V><<<p.fpGrid, SCGAL_BS, 0, s>>>(p, x, out);
         return;
     }
     if (p.phC) {
@@ -1485,6 +1619,7 @@ void phase_perm(const double* in, double* out, long long d, int n, int n1, int n
     template int prepare_phase_cluster<V>(const KP<V>&, int);                                             \
     template int phase_cluster_size<V>(int);                                                              \
     template void launch_phase_step<V>(const KP<V>&, int, cudaStream_t);                                  \
+    template void launch_fp_lanczos_update<V>(const KP<V>&, int, cudaStream_t);                           \
     template void launch_phase_update<V>(const KP<V>&, int, cudaStream_t);                                \
     template void launch_apply_D_phase<V>(const KP<V>&, const V*, V*, const typename VT<V>::R*, cudaStream_t); \
     template void launch_wvec_from_w<V>(const KP<V>&, int, const double*, cudaStream_t);

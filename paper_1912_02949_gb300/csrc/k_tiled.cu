@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(W * 32, W == 4 ? 7 : 4) k_tile_rows(KP<V> p, i
             }
         }
     }
-    if constexpr (STEP) step_dot<V, W * 32>(p, i, dacc.total());
+    if constexpr (STEP) step_dot<V, W * 32>(p, i, dacc);
 }
 
 // ---------------------------------------------------------------------------
