@@ -377,29 +377,6 @@ __device__ __forceinline__ bool grid_reduce(WT (&v)[NV], double* __restrict__ pa
     return grid_tail<NV, BS>(mine, partials, ticket, tot);
 }
 
-// Block-wide fixed-order sum of x[0..m) (every thread receives the total;
-// blockDim.x == BS).
-template <int BS = SCGAL_BS>
-__device__ __forceinline__ double block_sum_array(const double* x, int m) {
-    __shared__ double red[BS / 32];
-    __shared__ double res;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double s = 0.0;
-    s = strided_sum_cg<BS>(x, m, s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) red[wid] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < BS / 32; ++w) t += red[w];
-        res = t;
-    }
-    __syncthreads();
-    return res;
-}
-
 template <int NV, typename WT = double>
 __device__ __forceinline__ bool grid_reduce_2d(WT (&v)[NV], double* __restrict__ partials,
                                                unsigned* __restrict__ ticket, double* tot) {

@@ -139,8 +139,11 @@ struct StepScalars {
 template <typename V>
 __device__ __forceinline__ StepScalars step_scalars(const KP<V>& p, int i, double dot, double rr) {
     StepScalars r;
-    r.rho = (i > 0) ? sqrt(rr) : 0.0;
-    r.s = (i > 0) ? 1.0 / r.rho : p.sv[0];
+    // one reciprocal square root, then rho = rr / sqrt(rr): a shorter FP64
+    // dependency chain than a square root followed by a division
+    // (rr == 0, a breakdown, keeps rho == 0 exactly)
+    r.s = (i > 0) ? rsqrt(rr) : p.sv[0];
+    r.rho = (i > 0 && rr != 0.0) ? rr * r.s : 0.0;
     r.om = r.s * r.s * dot;
     return r;
 }
@@ -192,24 +195,12 @@ __device__ __forceinline__ void write_step_partial(double* partials, unsigned* t
     }
 }
 
-// The end of step i in the step kernel's last block (p.fin_upd == 0): the
-// previous update's ||W_i||^2 partials added up here; every thread of that
-// block (BS of them) calls it.
-template <typename V, int BS = SCGAL_BS>
-__device__ __forceinline__ void finish_lanczos_step(const KP<V>& p, int i, double dot);
-
 // The ||W||^2 partials of the update that formed W_i, for the end of step i
 // (double-buffered by step parity: the update of step i reads one buffer while
 // it writes the other).
 template <typename V>
 __device__ __forceinline__ double* upart_of(const KP<V>& p, int i) {
     return p.upart + (size_t)(i & 1) * p.upcap;
-}
-
-template <typename V, int BS>
-__device__ __forceinline__ void finish_lanczos_step(const KP<V>& p, int i, double dot) {
-    const double rr = (i > 0) ? block_sum_array<BS>(upart_of(p, i), p.nupd) : 0.0;
-    if (threadIdx.x == 0) finish_lanczos_scalars(p, i, dot, rr);
 }
 
 // A step kernel's <W_i, D W_i> (a CompSum or a double per thread): with
@@ -219,10 +210,63 @@ template <typename V, int BS, typename A>
 __device__ __forceinline__ void step_dot(const KP<V>& p, int i, const A& v) {
     if (p.fin_upd) {
         write_step_partial<BS>(p.partials, p.ticket, v);
-    } else {
-        const double bt = block_total<BS>(v);
-        __shared__ double tot[1];
-        if (grid_tail<1, BS>(bt, p.partials, p.ticket, tot)) finish_lanczos_step<V, BS>(p, i, tot[0]);
+        return;
+    }
+    // this block's partial, then a grid ticket; the last block adds up the
+    // step's partials and the previous update's ||W_i||^2 partials in one pass
+    // (both arrays' loads in flight together, each sum in index order) and
+    // ends the step
+    const double bt = block_total<BS>(v);
+    __shared__ bool last;
+    __shared__ double red[2][BS / 32];
+    const unsigned nblk = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) {
+        p.partials[bid] = bt;
+        __threadfence();   // this block's partial is visible before its ticket
+        last = (atomicAdd(p.ticket, 1u) == nblk - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int nd = (int)nblk, nu = (i > 0) ? p.nupd : 0;
+    const double* __restrict__ up = upart_of(p, i);
+    constexpr int U = 8;
+    double s1 = 0.0, s2 = 0.0;
+    for (int b0 = threadIdx.x; b0 < max(nd, nu); b0 += U * BS) {
+        double v1[U], v2[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int b = b0 + u * BS;
+            v1[u] = b < nd ? __ldcg(p.partials + b) : 0.0;
+            v2[u] = b < nu ? __ldcg(up + b) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (b0 + u * BS < nd) s1 += v1[u];
+            if (b0 + u * BS < nu) s2 += v2[u];
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+        red[0][wid] = s1;
+        red[1][wid] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double dot = 0.0, rr = 0.0;
+#pragma unroll
+        for (int w = 0; w < BS / 32; ++w) {
+            dot += red[0][w];
+            rr += red[1][w];
+        }
+        finish_lanczos_scalars(p, i, dot, rr);
+        *p.ticket = 0u;
     }
 }
 
@@ -232,9 +276,28 @@ __device__ __forceinline__ void step_dot(const KP<V>& p, int i, const A& v) {
 // FP64 additions few (they are scarce on GB300).
 template <typename V>
 __device__ __forceinline__ void step_sums_warp(const KP<V>& p, int i, double& dot, double& rr) {
-    const int nd = (int)__ldcg(p.ticket + 2);
-    double s1 = strided_sum_cg<32>(p.partials, nd);
-    double s2 = (i > 0) ? strided_sum_cg<32>(upart_of(p, i), p.nupd) : 0.0;
+    // the ptychography window kernel leaves exactly one partial per window
+    const int nd = (p.c.kind == KIND_PTYCHO) ? p.c.L : (int)__ldcg(p.ticket + 2);
+    const int nu = (i > 0) ? p.nupd : 0;
+    const double* __restrict__ up = upart_of(p, i);
+    // both arrays' loads in flight together; each sum keeps its index order
+    constexpr int U = 8;
+    double s1 = 0.0, s2 = 0.0;
+    const int lane = threadIdx.x & 31;
+    for (int b0 = lane; b0 < max(nd, nu); b0 += U * 32) {
+        double v1[U], v2[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int b = b0 + u * 32;
+            v1[u] = b < nd ? __ldcg(p.partials + b) : 0.0;
+            v2[u] = b < nu ? __ldcg(up + b) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (b0 + u * 32 < nd) s1 += v1[u];
+            if (b0 + u * 32 < nu) s2 += v2[u];
+        }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s1 += __shfl_down_sync(0xffffffffu, s1, o);
@@ -275,6 +338,7 @@ __device__ __forceinline__ void step_coeffs(const KP<V>& p, int i, typename VT<V
     typedef typename VT<V>::R Rt;
     __shared__ Rt co[3];
     if (threadIdx.x < 32) {
+        const double sprev = (i > 0 && threadIdx.x == 0) ? p.sv[i - 1] : 0.0;   // issued before the sums
         double si = 0.0, om = 0.0, rho = 0.0;
         if (p.fin_upd) {
             double dot, rr;
@@ -294,7 +358,7 @@ __device__ __forceinline__ void step_coeffs(const KP<V>& p, int i, typename VT<V
         if (threadIdx.x == 0) {
             co[0] = (Rt)si;
             co[1] = (Rt)(-om * si);
-            co[2] = (i > 0) ? (Rt)(-rho * p.sv[i - 1]) : (Rt)0;
+            co[2] = (i > 0) ? (Rt)(-rho * sprev) : (Rt)0;
         }
     }
     __syncthreads();
