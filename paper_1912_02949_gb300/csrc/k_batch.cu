@@ -46,7 +46,7 @@ constexpr int BATCH_QMAX = 320;           // largest Lanczos length (tridiagonal
 constexpr int BATCH_RMAX = 16;
 constexpr int YOFF = BATCH_NMAX_Y + 4;    // float offset of the second region (16-byte aligned)
 constexpr int LOFF = BATCH_NMAX + 4;      // float offset of the tridiagonal scratch when n > BATCH_NMAX_Y
-constexpr int TSM_BYTES = 5 * (int)sizeof(double) * (BATCH_QMAX + 1);
+constexpr int TSM_BYTES = 7 * (int)sizeof(double) * (BATCH_QMAX + 1);   // 6 double + 2 float arrays
 constexpr size_t BATCH_SMEM = sizeof(float) * 2 * (size_t)YOFF;
 static_assert(sizeof(float) * (size_t)LOFF + TSM_BYTES <= BATCH_SMEM, "scratch layout");
 static_assert(sizeof(float) * (size_t)YOFF >= TSM_BYTES, "scratch layout");

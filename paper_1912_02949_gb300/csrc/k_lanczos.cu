@@ -437,7 +437,7 @@ template <typename V> void launch_lanczos_update(const KP<V>& p, int grid, int i
     launch_pdl(k_lanczos_update<V>, p.nupd, SCGAL_BS, 0, s, p, i);
 }
 template <typename V> void launch_tridiag(const KP<V>& p, int q, cudaStream_t s) {
-    launch_pdl(k_tridiag<V>, 1, SCGAL_BS, 5 * (size_t)(q + 1) * sizeof(double), s, p, q);   // 4 double + 2 float arrays
+    launch_pdl(k_tridiag<V>, 1, SCGAL_BS, 7 * (size_t)(q + 1) * sizeof(double), s, p, q);   // 6 double + 2 float arrays
 }
 template <typename V> void launch_ritz(const KP<V>& p, int grid, cudaStream_t s) {
     const size_t sm = sizeof(double) * (size_t)(p.c.qmax + 1);  // Ritz coefficients, k <= qmax

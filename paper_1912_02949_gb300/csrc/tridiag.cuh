@@ -8,6 +8,54 @@
 
 namespace scgal {
 
+// Biased binary exponent of x (0 for zero and subnormals), by integer operations.
+__device__ __forceinline__ int tri_exp(double x) { return (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu); }
+// 2^j for -1022 <= j <= 1023, built from its bits.
+__device__ __forceinline__ double tri_pow2(int j) { return __hiloint2double((j + 1023) << 20, 0); }
+
+// Block-wide reductions over the values of entries 0..k-1 (entry i on thread
+// i mod NT; only the warps holding entries shuffle), the result for every
+// thread; red holds 32 doubles of shared memory, res one.  Fixed order.
+__device__ __forceinline__ double tri_block_sum(double v, double* red, double* res, int k, int NT) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nwa = (min(k, NT) + 31) >> 5;
+    if (wid < nwa) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = red[0];
+        for (int w = 1; w < nwa; ++w) t += red[w];
+        *res = t;
+    }
+    __syncthreads();
+    const double r = *res;
+    __syncthreads();   // red and res are free again
+    return r;
+}
+__device__ __forceinline__ unsigned long long tri_block_max(unsigned long long v, double* red, int k, int NT) {
+    unsigned long long* rb = reinterpret_cast<unsigned long long*>(red);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nwa = (min(k, NT) + 31) >> 5;
+    if (wid < nwa) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+        if (lane == 0) rb[wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = rb[0];
+        for (int w = 1; w < nwa; ++w) t = max(t, rb[w]);
+        rb[32 - 1] = t;   // nwa <= 32
+    }
+    __syncthreads();
+    const unsigned long long r = rb[32 - 1];
+    __syncthreads();
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // Minimum eigenpair of T = tridiag(rho, omega, rho), k x k, one block.
 //  1. Bracket: Sturm-count multisection in FP32 (each of the 256 threads counts
@@ -23,8 +71,14 @@ namespace scgal {
 //     root of a real-rooted polynomial, clusters included -- and xi = that root.
 //     FP32 path: sigma just below the FP32 bracket, and xi = the FP64 Rayleigh
 //     quotient of the FP64 eigenvector (its error is quadratic in the vector's).
-// The FP64 work is a few sequential passes over k: GB300's FP64 rate is low,
-// and a 256-thread FP64 bisection saturated the SM's FP64 pipe for ~1 ms.
+// GB300's FP64 rate is low (a 256-thread FP64 bisection saturated the SM's
+// FP64 pipe for ~1 ms), and an FP64 instruction costs about as much in one
+// lane as in 32, so the serial passes carry one or two FP64 operations per
+// entry and everything else runs across the block: the LU pivots come from
+// the three-term recurrence of the leading minors (pivot i = P_{i+1} / P_i,
+// no division on the serial chain; the reciprocals are taken in parallel),
+// the solves use precomputed multipliers (one FMA per entry and pass), and
+// the normalisation and the Rayleigh quotient are block reductions.
 // Then the stopping values of Eq. E.1 for the state of iteration t (before its
 // update), the LMO decision, and the iteration record.
 template <typename V>
@@ -34,11 +88,13 @@ __device__ void tridiag_body(const KP<V>& p, int q, double* smt) {
     const int k = sc->k;
     double* a = smt;
     double* e = a + k;
-    double* u = e + k;
-    double* m = u + k;
-    float* af = reinterpret_cast<float*>(m + k);
+    double* A1 = e + k;      // scratch: T - sigma I's diagonal, then minors, then l_i
+    double* A2 = A1 + k;     //          e_{i-1}^2, then minors, then g_i
+    double* m = A2 + k;      // 1 / pivot_i
+    double* u = m + k;       // the eigenvector
+    float* af = reinterpret_cast<float*>(u + k);
     float* e2f = af + k;
-    __shared__ double s_lo, s_hi, s_scale;
+    __shared__ double s_lo, s_hi, s_scale, s_sigma, s_xi, s_res;
     __shared__ int s_j;
     __shared__ double r_lo[32], r_hi[32];
     for (int i = threadIdx.x; i < k; i += NT) {
@@ -97,7 +153,7 @@ __device__ void tridiag_body(const KP<V>& p, int q, double* smt) {
             if (fabsf(dd) < pivf) dd = -pivf;
             cnt += dd < 0.0f;
             for (int i = 1; i < k; ++i) {
-                dd = (af[i] - x) - e2f[i - 1] / dd;
+                dd = (af[i] - x) - __fdividef(e2f[i - 1], dd);   // |dd| >= 1e-30, O(1) operands
                 if (fabsf(dd) < pivf) dd = -pivf;
                 cnt += dd < 0.0f;
             }
@@ -114,8 +170,12 @@ __device__ void tridiag_body(const KP<V>& p, int q, double* smt) {
             }
             __syncthreads();
         }
+        constexpr bool LAGUERRE = sizeof(typename VT<V>::R) == 8;
+        if constexpr (LAGUERRE) {
+            for (int i = threadIdx.x; i < k; i += NT) A2[i] = (i > 0) ? e[i - 1] * e[i - 1] : 0.0;
+            __syncthreads();
+        }
         if (threadIdx.x == 0) {
-            constexpr bool LAGUERRE = sizeof(typename VT<V>::R) == 8;
             double sigma;
             if constexpr (LAGUERRE) {
                 // FP64 path: Laguerre's iteration on p_k(x) of the scaled matrix, from
@@ -131,20 +191,21 @@ __device__ void tridiag_body(const KP<V>& p, int q, double* smt) {
                     double h0 = 0.0, h1 = 0.0;                    // second derivatives
                     for (int i = 1; i < k; ++i) {
                         const double ai = a[i] - x;
-                        const double e2 = e[i - 1] * e[i - 1];
+                        const double e2 = A2[i];                  // e_{i-1}^2
                         const double p2 = ai * p1 - e2 * p0;
                         const double d2 = ai * d1 - p1 - e2 * d0;
                         const double h2 = ai * h1 - 2.0 * d1 - e2 * h0;
                         p0 = p1; p1 = p2;
                         d0 = d1; d1 = d2;
                         h0 = h1; h1 = h2;
-                        const double mag = fmax(fabs(p1), fmax(fabs(d1), fabs(h1)));
-                        if (mag > 0x1p+400 || (mag < 0x1p-400 && mag > 0.0)) {
-                            int ex;
-                            frexp(mag, &ex);
-                            p0 = ldexp(p0, -ex); p1 = ldexp(p1, -ex);
-                            d0 = ldexp(d0, -ex); d1 = ldexp(d1, -ex);
-                            h0 = ldexp(h0, -ex); h1 = ldexp(h1, -ex);
+                        // the largest magnitude's exponent, by integer operations;
+                        // rescaling by a power of two is exact
+                        const int em = max(tri_exp(p1), max(tri_exp(d1), tri_exp(h1)));
+                        if (em > 1023 + 400 || (em < 1023 - 400 && em > 0)) {
+                            const double f = tri_pow2(1022 - em);
+                            p0 *= f; p1 *= f;
+                            d0 *= f; d1 *= f;
+                            h0 *= f; h1 *= f;
                         }
                     }
                     if (p1 == 0.0) break;                         // x is an eigenvalue
@@ -166,53 +227,106 @@ __device__ void tridiag_body(const KP<V>& p, int q, double* smt) {
                 // and the Rayleigh quotient below are FP64
                 sigma = s_lo - 2.0 * (s_hi - s_lo) - 64.0 * FLT_EPSILON;
             }
-            // inverse iteration on T - sigma I = L U, sigma below the smallest
-            // eigenvalue: U has the pivots m_i on its diagonal and e_i above it, L the
-            // multipliers l_i = e_{i-1} / m_{i-1} below its unit diagonal; m[] keeps 1 / m_i
-            const double tiny = DBL_EPSILON * 1e-3;
-            {
-                double mm = a[0] - sigma;
-                if (fabs(mm) < tiny) mm = tiny;
-                m[0] = 1.0 / mm;
+            s_sigma = sigma;
+            s_xi = xi;
+        }
+        __syncthreads();
+        const double sigma = s_sigma;
+        // inverse iteration on T - sigma I = L U, sigma below the smallest
+        // eigenvalue: U has the pivots d_i on its diagonal and e_i above it, L the
+        // multipliers l_i = e_{i-1} / d_{i-1} below its unit diagonal.  The pivots
+        // are ratios of leading principal minors, d_i = P_{i+1} / P_i with P_0 = 1,
+        // P_{i+1} = (a_i - sigma) P_i - e_{i-1}^2 P_{i-1}; a pivot below 2^-62
+        // (relative to P_i) is clamped there, as elimination would.
+        for (int i = threadIdx.x; i < k; i += NT) {
+            A1[i] = a[i] - sigma;
+            A2[i] = (i > 0) ? e[i - 1] * e[i - 1] : 0.0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double clamp = 0x1p-62;
+            double P0 = 1.0, P1 = A1[0];
+            if (tri_exp(P1) < 1023 - 62) P1 = clamp;
+            A1[0] = P0;
+            A2[0] = P1;
+            for (int i = 1; i < k; ++i) {
+                const double ci = A1[i], Ei = A2[i];
+                double P2 = fma(ci, P1, -Ei * P0);
+                if (tri_exp(P2) < tri_exp(P1) - 62) P2 = P1 * clamp;   // keeps the pivot positive
+                A1[i] = P1;                                             // minors of one scale
+                A2[i] = P2;
+                P0 = P1;
+                P1 = P2;
+                const int ex = tri_exp(P1);
+                if (ex > 1023 + 400 || ex < 1023 - 400) {               // rescale by a power of two
+                    const double f = tri_pow2(1023 - ex);
+                    P0 *= f;
+                    P1 *= f;
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < k; i += NT) m[i] = A1[i] / A2[i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < k; i += NT) {
+            A1[i] = (i > 0) ? e[i - 1] * m[i - 1] : 0.0;        // l_i
+            A2[i] = (i < k - 1) ? e[i] * m[i] : 0.0;            // g_i = e_i / d_i
+            u[i] = 1.0;
+        }
+        __syncthreads();
+        // three solves, then one normalisation: each solve grows u by at most
+        // 1 / min pivot (< 2^64 with the clamp at 2^-62), so u stays finite
+        for (int it = 0; it < 3; ++it) {
+            if (threadIdx.x == 0) {                              // L y = u
+                double up = u[0];
                 for (int i = 1; i < k; ++i) {
-                    const double es = e[i - 1];
-                    mm = (a[i] - sigma) - es * es * m[i - 1];
-                    if (fabs(mm) < tiny) mm = tiny;
-                    m[i] = 1.0 / mm;
+                    up = fma(-A1[i], up, u[i]);
+                    u[i] = up;
                 }
             }
-            // three solves, then one normalisation: each solve grows u by at most
-            // 1 / min pivot (< 2^64 with the clamp below 1e-19), so u stays finite
-            for (int i = 0; i < k; ++i) u[i] = 1.0;
-            for (int it = 0; it < 3; ++it) {
-                for (int i = 1; i < k; ++i) u[i] -= e[i - 1] * m[i - 1] * u[i - 1];
-                u[k - 1] *= m[k - 1];
-                for (int i = k - 2; i >= 0; --i) u[i] = (u[i] - e[i] * u[i + 1]) * m[i];
-            }
-            {
-                double mx = 0.0;
-                for (int i = 0; i < k; ++i) mx = fmax(mx, fabs(u[i]));
-                const double imx = 1.0 / mx;
-                double nrm = 0.0;
-                for (int i = 0; i < k; ++i) {
-                    u[i] *= imx;
-                    nrm += u[i] * u[i];
+            __syncthreads();
+            for (int i = threadIdx.x; i < k; i += NT) u[i] *= m[i];   // D^-1 y
+            __syncthreads();
+            if (threadIdx.x == 0) {                              // (I + D^-1 E) u = D^-1 y
+                double un = u[k - 1];
+                for (int i = k - 2; i >= 0; --i) {
+                    un = fma(-A2[i], un, u[i]);
+                    u[i] = un;
                 }
-                nrm = 1.0 / sqrt(nrm);
-                for (int i = 0; i < k; ++i) u[i] *= nrm;
             }
-            if constexpr (!LAGUERRE) {
-                // the Ritz value: FP64 Rayleigh quotient of the unit FP64 vector (its
-                // error is quadratic in the vector's)
-                double num = 0.0;
-                for (int i = 0; i < k; ++i) {
-                    double tu = a[i] * u[i];
-                    if (i > 0) tu += e[i - 1] * u[i - 1];
-                    if (i < k - 1) tu += e[i] * u[i + 1];
-                    num += u[i] * tu;
-                }
-                xi = num * scale;
+            __syncthreads();
+        }
+        // normalise: scale by the largest magnitude (an integer maximum of the
+        // bit patterns of |u_i|), then by the 2-norm of the scaled vector
+        {
+            unsigned long long mb = 0ull;
+            for (int i = threadIdx.x; i < k; i += NT)
+                mb = max(mb, (unsigned long long)__double_as_longlong(fabs(u[i])));
+            const double mx = __longlong_as_double((long long)tri_block_max(mb, r_lo, k, NT));
+            const double imx = 1.0 / mx;
+            double ss = 0.0;
+            for (int i = threadIdx.x; i < k; i += NT) {
+                const double v = u[i] * imx;
+                ss = fma(v, v, ss);
             }
+            const double nrm = tri_block_sum(ss, r_lo, &s_res, k, NT);
+            const double sc2 = imx * (1.0 / sqrt(nrm));
+            for (int i = threadIdx.x; i < k; i += NT) u[i] *= sc2;
+            __syncthreads();
+        }
+        if constexpr (sizeof(typename VT<V>::R) != 8) {
+            // the Ritz value: FP64 Rayleigh quotient of the unit FP64 vector (its
+            // error is quadratic in the vector's)
+            double num = 0.0;
+            for (int i = threadIdx.x; i < k; i += NT) {
+                double tu = a[i] * u[i];
+                if (i > 0) tu = fma(e[i - 1], u[i - 1], tu);
+                if (i < k - 1) tu = fma(e[i], u[i + 1], tu);
+                num = fma(u[i], tu, num);
+            }
+            xi = tri_block_sum(num, r_lo, &s_res, k, NT) * scale;
+        } else {
+            xi = s_xi;
         }
     }
     if (threadIdx.x == 0) {
