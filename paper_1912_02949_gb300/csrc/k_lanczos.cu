@@ -195,8 +195,13 @@ __global__ void __launch_bounds__(SCGAL_BS) k_tridiag(KP<V> p, int q) {
 // ---------------------------------------------------------------------------
 // Ritz vector v = sum_j coef_j W_j (unnormalised), ||v||^2 and r = v* Omega.
 // Each thread combines a 16-byte group of the basis rows (EPT elements).
+// stage: the stored Omega rows of a warp's 32 groups (contiguous, 32 W R
+// values) are read with coalesced 16-byte loads into the warp's slice of
+// shared memory, lane l's W R values at l (W R + 1) (an odd stride: the
+// lanes' reads fall in distinct banks), instead of R scalar loads per element
+// at a stride of W R values across the warp.
 template <typename V, int RT>
-__global__ void __launch_bounds__(SCGAL_BS) k_ritz(KP<V> p) {
+__global__ void __launch_bounds__(SCGAL_BS) k_ritz(KP<V> p, int stage) {
     typedef typename VT<V>::R Rt;
     constexpr bool CXV = VT<V>::cplx;
     constexpr int NV = 1 + (CXV ? 2 * RT : RT);
@@ -219,10 +224,25 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ritz(KP<V> p) {
     const size_t ldr = (size_t)p.ldb * CF;
     const Rt* __restrict__ B = reinterpret_cast<const Rt*>(p.basis);
     Rt* __restrict__ vb = reinterpret_cast<Rt*>(p.vbuf);
-    auto omega_acc = [&](int e, V v) {
+    const int LB = W * R;                                  // values of a lane's rows
+    const int lane = threadIdx.x & 31;
+    Rt* stg = reinterpret_cast<Rt*>(reinterpret_cast<unsigned char*>(smr) + ritz_cf_bytes(p.c.qmax)) +
+              (size_t)(threadIdx.x >> 5) * 32 * (LB + 1);
+    auto omega_acc = [&](int e, V v, const Rt* srow) {
         acc[0] += abs2(v);
         V orow[RT];
-        if (p.c.omega_regen) {
+        if (srow) {
+#pragma unroll
+            for (int c = 0; c < RT; ++c)
+                if (c < R) {
+                    if constexpr (CXV) {
+                        orow[c].x = srow[2 * c];
+                        orow[c].y = srow[2 * c + 1];
+                    } else {
+                        orow[c] = srow[c];
+                    }
+                }
+        } else if (p.c.omega_regen) {
             omega_row<RT>(p.c.seed, p.c.instance, e, R, orow);
         } else {
             const V* __restrict__ om = p.Omega + (size_t)e * R;
@@ -245,7 +265,23 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ritz(KP<V> p) {
     };
     const long long ng = n / EPT;
     const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
-    for (long long g = gt; g < ng; g += st) {
+    // warp-uniform loop (the staging is a warp-wide copy); st is a multiple of 32
+    for (long long gb = gt - lane; gb < ng; gb += st) {
+        const long long g = gb + lane;
+        if (stage) {
+            const long long nvec = min(32LL, ng - gb) * R;   // 16-byte vectors of the warp's rows
+            const RV* __restrict__ src = reinterpret_cast<const RV*>(reinterpret_cast<const Rt*>(p.Omega) + gb * LB);
+            __syncwarp();                                    // the previous rows are consumed
+            for (long long f = lane; f < nvec; f += 32) {
+                const RV ov = src[f];
+                const int j0 = (int)f * W;                   // a lane block holds whole vectors
+                Rt* d = stg + j0 + j0 / LB;
+#pragma unroll
+                for (int q = 0; q < W; ++q) d[q] = ov.v[q];
+            }
+            __syncwarp();
+        }
+        if (g >= ng) continue;
         RV s0, s1;
 #pragma unroll
         for (int q = 0; q < W; ++q) s0.v[q] = s1.v[q] = 0;
@@ -276,14 +312,14 @@ __global__ void __launch_bounds__(SCGAL_BS) k_ritz(KP<V> p) {
             } else {
                 v = s0.v[ee];
             }
-            omega_acc((int)(g * EPT + ee), v);
+            omega_acc((int)(g * EPT + ee), v, stage ? stg + lane * (LB + 1) + ee * R * CF : nullptr);
         }
     }
     for (long long e = ng * EPT + gt; e < n; e += st) {   // tail elements
         V v = vzero<V>();
         for (int j = 0; j < k; ++j) vaxpy(v, cf[j], p.basis[(size_t)j * p.ldb + e]);
         p.vbuf[e] = v;
-        omega_acc((int)e, v);
+        omega_acc((int)e, v, nullptr);
     }
     __shared__ double tot[NV];
     if (grid_reduce<NV, Rt>(acc, p.partials, p.ticket, tot)) {
@@ -402,12 +438,27 @@ template <typename V> int resident_update() {
     static const int r = resident_blocks(k_lanczos_update<V>, 0);
     return r;
 }
+// k_ritz's staging of the stored Omega: R <= 16 (wider rows would halve the
+// resident blocks), and its shared memory (coefficients, then 8 warps x 32
+// lanes x (W R + 1) values).
+template <typename V> int ritz_stage(const KP<V>& p) { return (!p.c.omega_regen && p.c.R <= 16) ? 1 : 0; }
+template <typename V> size_t ritz_smem(const KP<V>& p) {
+    typedef typename VT<V>::R Rt;
+    constexpr int W = 16 / sizeof(Rt);
+    size_t b = ritz_cf_bytes(p.c.qmax);
+    if (ritz_stage(p)) b += sizeof(Rt) * (size_t)SCGAL_BS * (W * p.c.R + 1);
+    return b;
+}
+template <typename V, int RT> int ritz_resident_rt(const KP<V>& p) {
+    // the limit only allows the launch; every handle's launch asks for its own size
+    cudaFuncSetAttribute(k_ritz<V, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return resident_blocks(k_ritz<V, RT>, ritz_smem(p));
+}
 template <typename V> int ritz_resident(const KP<V>& p) {
-    const size_t sm = sizeof(double) * (size_t)(p.c.qmax + 1);
-    if (p.c.R <= 4) return resident_blocks(k_ritz<V, 4>, sm);
-    if (p.c.R <= 8) return resident_blocks(k_ritz<V, 8>, sm);
-    if (p.c.R <= 16) return resident_blocks(k_ritz<V, 16>, sm);
-    return resident_blocks(k_ritz<V, 32>, sm);
+    if (p.c.R <= 4) return ritz_resident_rt<V, 4>(p);
+    if (p.c.R <= 8) return ritz_resident_rt<V, 8>(p);
+    if (p.c.R <= 16) return ritz_resident_rt<V, 16>(p);
+    return ritz_resident_rt<V, 32>(p);
 }
 template <typename V> void prepare_lanczos_shapes() {
     (void)resident_dual<V>();
@@ -440,12 +491,13 @@ template <typename V> void launch_tridiag(const KP<V>& p, int q, cudaStream_t s)
     launch_pdl(k_tridiag<V>, 1, SCGAL_BS, 7 * (size_t)(q + 1) * sizeof(double), s, p, q);   // 6 double + 2 float arrays
 }
 template <typename V> void launch_ritz(const KP<V>& p, int grid, cudaStream_t s) {
-    const size_t sm = sizeof(double) * (size_t)(p.c.qmax + 1);  // Ritz coefficients, k <= qmax
+    const size_t sm = ritz_smem(p);
+    const int stage = ritz_stage(p);
     // the caller caps grid at ritz_resident() (one wave)
-    if (p.c.R <= 4) launch_pdl(k_ritz<V, 4>, grid, SCGAL_BS, sm, s, p);
-    else if (p.c.R <= 8) launch_pdl(k_ritz<V, 8>, grid, SCGAL_BS, sm, s, p);
-    else if (p.c.R <= 16) launch_pdl(k_ritz<V, 16>, grid, SCGAL_BS, sm, s, p);
-    else launch_pdl(k_ritz<V, 32>, grid, SCGAL_BS, sm, s, p);
+    if (p.c.R <= 4) launch_pdl(k_ritz<V, 4>, grid, SCGAL_BS, sm, s, p, stage);
+    else if (p.c.R <= 8) launch_pdl(k_ritz<V, 8>, grid, SCGAL_BS, sm, s, p, stage);
+    else if (p.c.R <= 16) launch_pdl(k_ritz<V, 16>, grid, SCGAL_BS, sm, s, p, stage);
+    else launch_pdl(k_ritz<V, 32>, grid, SCGAL_BS, sm, s, p, stage);
 }
 template <typename V> void launch_gen_omega(const KP<V>& p, int grid, cudaStream_t s) {
     k_gen_omega<V><<<grid, SCGAL_BS, 0, s>>>(p);
