@@ -72,10 +72,31 @@ def lanczos_step_bytes(n: int, nnz: int) -> int:
     return 8 * nnz + 32 * n
 
 
-def kernel_source_sha() -> str:
+# The source of the Lanczos step's kernels: the files of the two tiled passes
+# and the CSR kernel, the shared helpers, and, of k_lanczos.cu, the update
+# kernel and its launch shape (the file's other kernels are not in the step).
+STEP_REGIONS = (("// With p.fin_upd the update first ends step i", "// With p.fin_upd, ends the run's last step"),
+                ("// Blocks of the update: enough for one round", "template <typename V> void launch_tridiag"))
+
+
+def step_source(lanczos_text: str) -> str:
+    parts = []
+    for a, b in STEP_REGIONS:
+        i = lanczos_text.index(a)
+        parts.append(lanczos_text[i:lanczos_text.index(b, i)])
+    return "".join(parts)
+
+
+def kernel_source_sha(read=None) -> str:
+    """sha256 prefix of the Lanczos step's kernel source (read(name) -> text,
+    default: the files in the tree)."""
+    if read is None:
+        def read(name):
+            return open(os.path.join(ROOT, "paper_1912_02949_gb300", "csrc", name), encoding="utf-8").read()
     h = hashlib.sha256()
-    for f in ("k_tiled.cu", "k_lanczos.cu", "k_maxcut.cu", "common.cuh", "internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1912_02949_gb300", "csrc", f), "rb").read())
+    for f in ("k_tiled.cu", "k_maxcut.cu", "common.cuh", "internal.h"):
+        h.update(read(f).encode())
+    h.update(step_source(read("k_lanczos.cu")).encode())
     return h.hexdigest()[:16]
 
 

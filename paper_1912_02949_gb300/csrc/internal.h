@@ -195,11 +195,6 @@ __device__ __forceinline__ void write_step_partial(double* partials, unsigned* t
     }
 }
 
-// Bytes of k_ritz's coefficient array (k <= qmax doubles), rounded up to 16.
-__host__ __device__ __forceinline__ size_t ritz_cf_bytes(int qmax) {
-    return (sizeof(double) * (size_t)(qmax + 1) + 15) / 16 * 16;
-}
-
 // The ||W||^2 partials of the update that formed W_i, for the end of step i
 // (double-buffered by step parity: the update of step i reads one buffer while
 // it writes the other).

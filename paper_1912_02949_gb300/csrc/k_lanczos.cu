@@ -193,6 +193,11 @@ __global__ void __launch_bounds__(SCGAL_BS) k_tridiag(KP<V> p, int q) {
 }
 
 // ---------------------------------------------------------------------------
+// Bytes of k_ritz's coefficient array (k <= qmax doubles), rounded up to 16.
+__host__ __device__ __forceinline__ size_t ritz_cf_bytes(int qmax) {
+    return (sizeof(double) * (size_t)(qmax + 1) + 15) / 16 * 16;
+}
+
 // Ritz vector v = sum_j coef_j W_j (unnormalised), ||v||^2 and r = v* Omega.
 // Each thread combines a 16-byte group of the basis rows (EPT elements).
 // stage: the stored Omega rows of a warp's 32 groups (contiguous, 32 W R
