@@ -80,10 +80,15 @@ STEP_REGIONS = (("// With p.fin_upd the update first ends step i", "// With p.fi
 
 
 def step_source(lanczos_text: str) -> str:
+    """The step's regions of k_lanczos.cu; the whole file if a marker is gone
+    (the hash then no longer matches a stored capture, which is the safe side)."""
     parts = []
     for a, b in STEP_REGIONS:
-        i = lanczos_text.index(a)
-        parts.append(lanczos_text[i:lanczos_text.index(b, i)])
+        i = lanczos_text.find(a)
+        j = lanczos_text.find(b, i) if i >= 0 else -1
+        if j < 0:
+            return lanczos_text
+        parts.append(lanczos_text[i:j])
     return "".join(parts)
 
 
