@@ -11,7 +11,7 @@ import pytest
 
 import workloads as W
 from oracle.cgal_dense import dense_maxcut, dense_phase, operator_norm
-from oracle.problems import MaxCutProblem, PhaseProblem
+from oracle.problems import MaxCutProblem, PhaseProblem, PtychoProblem
 
 
 def _rng(s=0):
@@ -50,18 +50,24 @@ def test_laplacian_quadratic_form_is_cut():
     assert math.isclose(-chi @ prob.C_apply(chi), cut, abs_tol=1e-9)
 
 
-@pytest.mark.parametrize("prob_kind", ["maxcut", "phase"])
+@pytest.mark.parametrize("prob_kind", ["maxcut", "phase", "ptycho"])
 def test_adjoint_identity(prob_kind):
-    """u*(A* z) u = <z, A(u u*)>  (Eq. 2.1)."""
+    """u*(A* z) u = <z, A(u u*)>  (Eq. 2.1).  For ptychography this is the
+    identity the Lanczos step's <x, D x> is formed from: sC ||x||^2 plus the
+    weighted squared window transforms, without the assembled D x."""
     r = _rng(5)
     if prob_kind == "maxcut":
         g = W.er_graph(64, 300, seed=1, weights="pm1")
         prob = MaxCutProblem(g.n, g.i, g.j, g.w)
         u = r.standard_normal(g.n)
-    else:
+    elif prob_kind == "phase":
         pd = W.phase_problem(32, 12, seed=1)
         prob = PhaseProblem(pd.masks, pd.b)
         u = r.standard_normal(32) + 1j * r.standard_normal(32)
+    else:
+        pd = W.ptycho_problem(24, 8, 3, seed=1)
+        prob = PtychoProblem(24, 8, 3, pd.pupil, pd.b)
+        u = r.standard_normal(prob.n) + 1j * r.standard_normal(prob.n)
     z = r.standard_normal(prob.d)
     lhs = np.vdot(u, prob.Astar_apply(z, u))
     rhs = np.dot(z, prob.A_of_uu(u))
