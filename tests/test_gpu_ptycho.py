@@ -94,6 +94,25 @@ def test_full_size_first_iterations(S):
         assert abs(rg["p"] - rr["p_orig"]) <= 1e-9 * max(abs(rr["p_orig"]), 1e-3)
 
 
+@pytest.mark.parametrize("prec", [32, 64])
+def test_deep_window_overlap_first_iterations(S, prec):
+    """Step s = 1: every pixel lies in M = 8 windows per dimension, more than the
+    Lanczos update keeps in registers, so it sums them in its loop; the first
+    two iterations step for step against the oracle."""
+    N, M, s, T = 16, 8, 1, 2
+    pd, h, prob = _pair(S, N, M, s, prec, T_max=100)
+    ref = sketchy_cgal(prob, R=5, T=T, seed=0)
+    S.scgal_solve(h, T)
+    # FP32: the first iteration (its q = 6 Lanczos steps all take the loop),
+    # where the Ritz value is not near zero
+    tol = 1e-9 if prec == 64 else TOL_XI[32]
+    steps = T if prec == 64 else 1
+    for rg, rr in zip(S.scgal_history(h, 1, steps), ref.history[:steps]):
+        assert rg["q"] == rr["q"]
+        assert abs(rg["xi"] - rr["xi"]) <= tol * abs(rr["xi"])
+        assert abs(rg["p"] - rr["p_orig"]) <= tol * max(abs(rr["p_orig"]), 1e-3)
+
+
 def test_state_roundtrip_natural_order(S):
     pd, h, prob = _pair(S, 16, 8, 4, 64)
     r = np.random.default_rng(1)
